@@ -1,0 +1,127 @@
+"""Multigrid setup and Rayleigh quotient iteration (Algorithm 1), FP64 oracle.
+
+Setup (Sec. 2.1, the paragraph after Algorithm 1): a few smoother iterations
+on random vectors give the first test vectors and P; then, a few times, one
+multigrid iteration is applied to every test vector, the test vectors are
+orthonormalised again and P and the coarse operator are rebuilt.  The smoother
+iterations on a random w approximate Q^-1 w (SAP: D x = gamma5 w from x = 0);
+one multigrid iteration on w is w <- B w with B the two-grid preconditioner at
+sigma = 0.
+
+Before the iteration the test vectors are rotated to the Ritz vectors of Q in
+their span and ordered by |theta| (same span, hence the same P); the first
+N_eig are the start vectors v_i of Algorithm 1.
+
+Algorithm 1, per sweep over the unconverged i:
+    sigma   = lambda_i * max(1 - eps_i, 0)                 (damped shift)
+    v_i    <- (Q - sigma)^-1 v_i                           (FGMRES + two-grid, FP64)
+    v_i    <- v_i - sum_{j<i} <v_j|v_i> v_j                 (classical GS, done twice)
+    v_i    <- v_i / ||v_i||
+    update v_i in P (rebuild P and the coarse operator)
+    lambda_i = <v_i|Q|v_i>,  eps_i = ||Q v_i - lambda_i v_i||
+starting from lambda_i = 0, eps_i = 1.  P is built from [v_1..v_N_eig] followed by
+the remaining test vectors when N_tv > N_eig.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dirac, krylov, mg
+
+
+def orthonormalise(W: np.ndarray) -> np.ndarray:
+    """Gram-Schmidt (each step twice) of the vectors W[0], W[1], ..."""
+    out = []
+    for w in W:
+        w = w.copy()
+        for _ in range(2):
+            for v in out:
+                w = w - np.vdot(v, w) * v
+        out.append(w / dirac.norm(w))
+    return np.array(out)
+
+
+def setup(op: dirac.WilsonClover, W0: np.ndarray, params: dict):
+    """Test vectors after the setup; returns (W, two-grid preconditioner)."""
+    p = params
+    W = []
+    if p["smoother"] == "sap":
+        sap = mg.SAP(op, p["sap_block"])
+        for w in W0:
+            W.append(sap.smooth(dirac.gamma5(w), np.zeros_like(w), 0.0, p["setup_smooth"], p["sap_mr_iters"]))
+    else:
+        for w in W0:
+            x, _ = krylov.gmres(op.Q, w, tol=0.0, restart=p["gmres_smooth_k"],
+                                maxiter=p["gmres_smooth_k"] * p["setup_smooth"])
+            W.append(x)
+    W = orthonormalise(np.array(W))
+    B = mg.TwoGrid(op, W, p)
+    for _ in range(p["setup_iters"]):
+        W = orthonormalise(np.array([B(w, 0.0) for w in W]))
+        B.set_test_vectors(W)
+    return W, B
+
+
+def ritz_rotate(op: dirac.WilsonClover, W: np.ndarray):
+    """Ritz vectors of Q in span(W), ordered by |theta| then theta."""
+    QW = np.array([op.Q(w) for w in W])
+    n = W.shape[0]
+    H = np.einsum("ia,ja->ij", np.conj(W.reshape(n, -1)), QW.reshape(n, -1))
+    H = 0.5 * (H + H.conj().T)
+    th, Y = np.linalg.eigh(H)
+    order = np.lexsort((th, np.abs(th)))
+    th, Y = th[order], Y[:, order]
+    return np.einsum("ij,i...->j...", Y, W), th
+
+
+def rayleigh(op: dirac.WilsonClover, v: np.ndarray):
+    Qv = op.Q(v)
+    lam = float(np.real(np.vdot(v, Qv)))
+    return lam, dirac.norm(Qv - lam * v)
+
+
+def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
+        n_eig: int, eps: float, params: dict, max_sweeps: int = 50, log=None):
+    """Algorithm 1.  Returns (lambda, vectors, eps_i, stats), sorted by |lambda|."""
+    p = params
+    V = [v.copy() for v in V[:n_eig]]
+    lam = np.zeros(n_eig)
+    res = np.ones(n_eig)
+    stats = dict(sweeps=0, solves=0, outer_iters=0)
+
+    def rebuild():
+        W = np.array(V + ([] if extra is None else list(extra)))
+        B.set_test_vectors(W)
+
+    rebuild()
+    while np.any(res > eps) and stats["sweeps"] < max_sweeps:
+        stats["sweeps"] += 1
+        for i in range(n_eig):
+            if res[i] <= eps:
+                continue
+            sigma = lam[i] * max(1.0 - res[i], 0.0)
+            x, info = krylov.fgmres(lambda v: op.Q_sigma(v, sigma), lambda r: B(r, sigma), V[i],
+                                    tol=p["solve_tol"], restart=p["outer_restart"], maxiter=p["outer_maxiter"])
+            stats["solves"] += 1
+            stats["outer_iters"] += info["iters"]
+            for _ in range(2):
+                coeff = [np.vdot(V[j], x) for j in range(i)]
+                for j in range(i):
+                    x = x - coeff[j] * V[j]
+            V[i] = x / dirac.norm(x)
+            rebuild()
+            lam[i], res[i] = rayleigh(op, V[i])
+            if log is not None:
+                log(f"sweep {stats['sweeps']} i={i} sigma={sigma:.6e} lambda={lam[i]:.12e} eps={res[i]:.3e} "
+                    f"outer={info['iters']}")
+    order = np.lexsort((lam, np.abs(lam)))
+    return lam[order], np.array(V)[order], res[order], stats
+
+
+def eigensolve(op: dirac.WilsonClover, W0: np.ndarray, n_eig: int, eps: float, params: dict,
+               max_sweeps: int = 50, log=None):
+    """Setup, Ritz rotation of the test vectors, then Algorithm 1."""
+    W, B = setup(op, W0, params)
+    W, _ = ritz_rotate(op, W)
+    extra = W[n_eig:] if W.shape[0] > n_eig else None
+    return rqi(op, W[:n_eig], extra, B, n_eig, eps, params, max_sweeps, log)
