@@ -1,0 +1,245 @@
+/*
+ * mgeig.h -- C ABI of libmgeig, a single-GPU (GB300, sm_103a) multigrid Rayleigh
+ * quotient eigensolver for the Hermitian clover-improved Wilson operator.
+ *
+ * Method: Bali, Collins, Frommer, Kahl, Kanamori, Mueller, Rottmann, Simeth,
+ * "(Approximate) Low-Mode Averaging with a new Multigrid Eigensolver",
+ * arXiv:1509.06865 (Lattice 2015).  Section and equation numbers below refer
+ * to that paper.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Lattice dims[4] = {Lx, Ly, Lz, Lt}; V = Lx*Ly*Lz*Lt sites.  Site index
+ *    s = ((t*Lz + z)*Ly + y)*Lx + x.
+ *  - Host gauge field: complex128 U[t][z][y][x][mu][a][b] (mu = 0..3 for
+ *    x, y, z, t), stored as interleaved (re, im) doubles: V*4*9 complex numbers.
+ *  - Host spinor field: complex128 psi[t][z][y][x][spin][colour], V*12 complex.
+ *    Chiral gamma basis with gamma5 = -g1 g2 g3 g4 = diag(1, 1, -1, -1) (Sec. 2).
+ *  - The operator (Sec. 2; the paper does not print D, this is the standard
+ *    form, mass normalisation, Wilson r = 1):
+ *      D psi(x) = (4 + m0) psi(x)
+ *               - 1/2 sum_mu [(1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu)]
+ *               + c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}(x) psi(x),
+ *    with the four-leaf clover F = (Q_{mu nu} - Q_{mu nu}^dag)/8, sigma = (i/2)[g_mu, g_nu],
+ *    g_k = [[0, i s_k], [-i s_k, 0]], g_4 = [[0, 1], [1, 0]].
+ *    Q = gamma5 D (Hermitian), D_sigma = D - sigma gamma5 = gamma5 (Q - sigma).
+ *    bc[mu] = +1 (periodic) or -1 (antiperiodic) multiplies every hop across
+ *    the lattice edge in direction mu.
+ *  - Every call returns MGEIG_OK (0) or a negative status; mgeig_strerror()
+ *    names it.  Host buffers stay owned by the caller; the library copies in
+ *    and out and never keeps a caller pointer.  The context owns all device
+ *    memory (allocated in mgeig_create / mgeig_set_params / mgeig_setup) and
+ *    frees it in mgeig_destroy.  A context is bound to one device and one
+ *    CUDA stream; calls on one context must not overlap.
+ */
+#ifndef MGEIG_H
+#define MGEIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MGEIG_OK 0
+#define MGEIG_EINVAL (-1)      /* bad argument, size or parameter                       */
+#define MGEIG_ENOTSETUP (-2)   /* gauge field or multigrid setup missing                */
+#define MGEIG_ECUDA (-3)       /* a CUDA runtime call failed                            */
+#define MGEIG_ENOCONV (-4)     /* iteration cap hit; outputs hold the best iterate      */
+#define MGEIG_EBREAKDOWN (-5)  /* NaN/Inf or a zero Krylov vector where none may appear */
+#define MGEIG_ENOMEM (-6)      /* device allocation failed                              */
+#define MGEIG_ETIMEOUT (-7)    /* a bounded device-side wait expired (grid barrier)     */
+
+/* precision of the multigrid preconditioner (Sec. 2.2: double precision FGMRES
+ * around a single precision multigrid method) */
+#define MGEIG_FP64 0   /* every level in FP64                                    */
+#define MGEIG_MIXED 1  /* FP32 smoother / P / coarse solve, FP64 outer and RQI    */
+
+/* smoother of the two-grid cycle (Sec. 2) */
+#define MGEIG_SAP 0    /* SAP on D_sigma with right-hand side gamma5 r            */
+#define MGEIG_GMRES 1  /* restarted GMRES(k) on Q - sigma                         */
+
+/* operator selector of mgeig_apply */
+#define MGEIG_OP_Q 0   /* y = (Q - sigma) x                                       */
+#define MGEIG_OP_D 1   /* y = (D - sigma gamma5) x                                */
+
+/* arithmetic of mgeig_apply */
+#define MGEIG_PREC_F64 0
+#define MGEIG_PREC_F32 1
+
+typedef struct mgeig_ctx mgeig_ctx;
+
+/* Solver parameters.  The paper fixes none of the smoother, coarse-grid and
+ * setup parameters (it cites the DD-alpha-AMG papers); mgeig_default_params
+ * fills in the values this library uses. */
+typedef struct mgeig_params {
+    double m0;            /* bare mass                                          */
+    double csw;           /* clover coefficient c_sw                            */
+    int bc[4];            /* fermion boundary phase per direction, +1 or -1     */
+    int agg[4];           /* aggregate extent per direction (divides dims)      */
+    int n_tv;             /* test vectors N_tv (2..24); coarse blocks 2N_tv^2   */
+    int sap_block[4];     /* SAP block extent; an even number >= 2 of blocks    */
+    int sap_cycles;       /* post-smoothing SAP cycles nu                       */
+    int sap_mr_iters;     /* minimal-residual steps per block solve             */
+    int smooth_steps;     /* GMRES smoother: restarts nu                        */
+    int gmres_smooth_k;   /* GMRES smoother: Krylov steps per restart           */
+    int setup_smooth;     /* setup: smoother iterations on the random vectors   */
+    int setup_iters;      /* setup: multigrid iterations per test vector        */
+    int outer_restart;    /* FGMRES restart length                              */
+    int outer_maxiter;    /* FGMRES iteration cap per solve                     */
+    int coarse_restart;   /* coarse GMRES restart length                        */
+    int coarse_maxiter;   /* coarse GMRES iteration cap per solve               */
+    double coarse_tol;    /* coarse GMRES relative residual                     */
+    double solve_tol;     /* FGMRES relative residual of each shifted solve     */
+    int precision;        /* MGEIG_FP64 or MGEIG_MIXED                          */
+    int smoother;         /* MGEIG_SAP or MGEIG_GMRES                           */
+    int max_sweeps;       /* Rayleigh quotient iteration: sweep cap             */
+    int n_guard;          /* extra iterated vectors beyond n_eig (capped at
+                             n_tv - n_eig); -1 = min(n_tv - n_eig, n_eig)       */
+} mgeig_params;
+
+/* Work counters and timings of the last setup / eigensolve / solve call. */
+typedef struct mgeig_stats {
+    int sweeps;           /* Algorithm 1 while-loop passes                      */
+    int solves;           /* shifted solves (Algorithm 1, v <- (Q - sigma)^-1 v)*/
+    int outer_iters;      /* FGMRES iterations                                  */
+    int mg_cycles;        /* two-grid preconditioner applications               */
+    long long coarse_iters;   /* coarse GMRES iterations                        */
+    long long fine_applies;   /* fine stencil applications (both precisions)    */
+    double seconds;       /* wall time of the call                              */
+} mgeig_stats;
+
+/* Fill p with the library defaults (m0 = 0, c_sw = 1, periodic, 4^4 aggregates,
+ * N_tv = 20, SAP 4^4 blocks, 3 cycles x 4 MR steps, mixed precision). */
+void mgeig_default_params(mgeig_params *p);
+
+/* Create a context for an Lx x Ly x Lz x Lt lattice on CUDA device `device`.
+ * Requires every extent >= 2.  *out receives the context (NULL on error). */
+int mgeig_create(mgeig_ctx **out, const int dims[4], int device);
+
+/* Free every device buffer and the context.  NULL is accepted. */
+void mgeig_destroy(mgeig_ctx *ctx);
+
+/* Validate and store parameters; (re)builds the clover term when a gauge field
+ * is loaded and drops an existing multigrid setup.  EINVAL names no field: the
+ * checks are agg/sap_block dividing dims, an even number >= 2 of SAP blocks per
+ * direction, 2 <= n_tv <= 24, bc = +-1, positive iteration counts. */
+int mgeig_set_params(mgeig_ctx *ctx, const mgeig_params *p);
+
+/* Copy a host gauge field (layout above) to the device and build the clover
+ * term from it (four-leaf clover, FP64, Sec. 2 / the operator above). */
+int mgeig_load_gauge(mgeig_ctx *ctx, const double *U);
+
+/* Same as mgeig_load_gauge for a gauge field already in device memory (same
+ * host layout, complex128), e.g. a buffer allocated with mgeig_alloc_dev. */
+int mgeig_load_gauge_dev(mgeig_ctx *ctx, const void *U_dev);
+
+/* Copy the clover term A(x) = c_sw (i/4) sum sigma F (without the mass term) to
+ * host memory as complex128 [site][chirality 2][6][6]; row/col = 3*spin' + colour
+ * with spin' = spin mod 2 inside the chirality block. */
+int mgeig_get_clover(mgeig_ctx *ctx, double *A);
+
+/* y = (Q - sigma) x (op = MGEIG_OP_Q) or (D - sigma gamma5) x (MGEIG_OP_D) for
+ * nrhs host spinors stored one after another, computed in FP64 or in FP32
+ * (inputs rounded to FP32, result widened back).  Fine stencil, Sec. 2. */
+int mgeig_apply(mgeig_ctx *ctx, double sigma, int op, int prec,
+                const double *x, double *y, int nrhs);
+
+/* Same on device memory: x, y are device spinors in the library's internal
+ * layout (FP64: double2 [12][V]; FP32: float4 [6][V], component k = 3*spin +
+ * colour, float4 q holds components 2q, 2q+1), one field each.  Launched on the
+ * context's stream, asynchronous.  For timing the stencil without copies. */
+int mgeig_apply_dev(mgeig_ctx *ctx, double sigma, int op, int prec,
+                    const void *x, void *y);
+
+/* Device buffer of `bytes` bytes owned by the context (freed by destroy), e.g.
+ * for mgeig_apply_dev operands.  *ptr = NULL on error. */
+int mgeig_alloc_dev(mgeig_ctx *ctx, size_t bytes, void **ptr);
+
+/* Convert n_fields host-layout complex128 spinors (host memory) into the
+ * internal device layout of precision prec at dev (mgeig_apply_dev layout). */
+int mgeig_pack_spinors(mgeig_ctx *ctx, int prec, const double *host, void *dev, int n_fields);
+
+/* Inverse of mgeig_pack_spinors: n_fields internal-layout device spinors of
+ * precision prec -> host-layout complex128 spinors in host memory. */
+int mgeig_unpack_spinors(mgeig_ctx *ctx, int prec, const void *dev, double *host, int n_fields);
+
+/* Multigrid setup (Sec. 2.1, paragraph after Algorithm 1): N_tv random test
+ * vectors (Philox4x32-10 uniforms, key = seed, counters (site, pair, vector,
+ * 0x5EED0001)), setup_smooth smoother iterations each, then setup_iters times
+ * {one two-grid iteration per test vector at sigma = 0; Gram-Schmidt in FP64;
+ * rebuild P and the coarse operator}. */
+int mgeig_setup(mgeig_ctx *ctx, uint64_t seed, mgeig_stats *stats);
+
+/* Replace the test vectors with n_tv host spinors and rebuild P and the coarse
+ * operator from them (no orthonormalisation across vectors). */
+int mgeig_set_test_vectors(mgeig_ctx *ctx, const double *W);
+
+/* Copy the current test vectors (n_tv host spinors, FP64) out. */
+int mgeig_get_test_vectors(mgeig_ctx *ctx, double *W);
+
+/* Interpolation P (Eq. 2.4): the n_tv fine spinors whose restriction to each
+ * aggregate and chirality are the orthonormal columns of P. */
+int mgeig_get_interp(mgeig_ctx *ctx, double *P);
+
+/* Coarse operator D_c = P^dag D P (Eq. 2.5) as complex128
+ * [direction 9][coarse site][2 n_tv][2 n_tv]; direction 0 = self, 1 + 2 mu =
+ * +mu, 2 + 2 mu = -mu; row/col = c*n_tv + j (chirality c, test vector j). */
+int mgeig_get_coarse_op(mgeig_ctx *ctx, double *Dc);
+
+/* r_c = P^dag r (host fine spinor -> host coarse vector [coarse site][2][n_tv]). */
+int mgeig_restrict(mgeig_ctx *ctx, const double *r, double *rc);
+
+/* e = P e_c (host coarse vector -> host fine spinor). */
+int mgeig_prolong(mgeig_ctx *ctx, const double *ec, double *e);
+
+/* y_c = (gamma5^c D_c - sigma) x_c = (Q_c - sigma) x_c (Eq. 2.6). */
+int mgeig_coarse_apply(mgeig_ctx *ctx, double sigma, const double *xc, double *yc);
+
+/* cycles SAP cycles (red then black blocks, sap_mr_iters MR steps per block)
+ * for D_sigma z = b from z (both host spinors; z updated in place). */
+int mgeig_sap(mgeig_ctx *ctx, double sigma, const double *b, double *z, int cycles);
+
+/* One two-grid preconditioner application z = B r at shift sigma (Eq. 2.3
+ * with no pre- and nu post-smoothing steps): coarse GMRES on Q_c - sigma (tol,
+ * coarse_maxiter), prolongation, then the smoother.  Host spinors. */
+int mgeig_mg_cycle(mgeig_ctx *ctx, double sigma, const double *r, double *z);
+
+/* Solve (Q - sigma) x = b with FP64 flexible GMRES preconditioned by the two-grid
+ * method (Sec. 2.2) to relative residual tol.  ENOCONV if outer_maxiter is hit. */
+int mgeig_solve(mgeig_ctx *ctx, double sigma, const double *b, double *x, double tol,
+                mgeig_stats *stats);
+
+/* Algorithm 1: the n_eig eigenpairs of Q of smallest |lambda| to eigen-residual
+ * ||Q v - lambda v|| <= tol, starting from the setup's test vectors (rotated to
+ * Ritz vectors of Q in their span, ordered by |theta|).  The iteration runs on
+ * n_eig + n_guard vectors and returns the n_eig of smallest |lambda|: the guard
+ * vectors lower the chance that a wanted mode is missed (the failure noted in
+ * Sec. 2.1 after Algorithm 1).  Needs mgeig_setup.
+ * Outputs (any may be NULL): evals[n_eig], evecs[n_eig host spinors, unit norm,
+ * phase such that the largest-modulus component is real positive],
+ * resid[n_eig]; sorted by |lambda| ascending, then lambda.  n_eig <= n_tv.
+ * ENOCONV when max_sweeps is hit (outputs hold the current iterates). */
+int mgeig_eigensolve(mgeig_ctx *ctx, int n_eig, double tol, double *evals, double *evecs,
+                     double *resid, mgeig_stats *stats);
+
+/* Per-kernel timing with CUDA events on the context stream (off by default;
+ * switching it on or off resets the counters).  mgeig_kernel_times returns,
+ * for kernel class k < n, the number of launches[k], their total device time
+ * ms[k] (0 while timing is off) and the total algorithmic bytes[k] they move
+ * (the bytes a perfect kernel would read and write once); names[k] is a static
+ * string.  Returns the number of classes, or a negative status. */
+int mgeig_set_timing(mgeig_ctx *ctx, int on);
+int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms,
+                       double *bytes, const char **names);
+
+/* Name of a status code. */
+const char *mgeig_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGEIG_H */

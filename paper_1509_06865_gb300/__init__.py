@@ -1,0 +1,11 @@
+"""GB300-native multigrid Rayleigh quotient eigensolver for the Hermitian
+clover-improved Wilson operator Q = gamma5 D (arXiv:1509.06865).
+
+The compute path is libmgeig.so (hand-written CUDA for sm_103a behind the C ABI
+in include/mgeig.h); ``Context`` is its ctypes binding.
+"""
+from ._lib import (EBREAKDOWN, EINVAL, ENOCONV, ENOTSETUP, FP64, GMRES, MIXED, OP_D, OP_Q, PREC_F32, PREC_F64, SAP,
+                   Context, MgeigError, load)
+
+__all__ = ["Context", "MgeigError", "load", "FP64", "MIXED", "SAP", "GMRES", "OP_Q", "OP_D", "PREC_F64",
+           "PREC_F32", "EINVAL", "ENOTSETUP", "ENOCONV", "EBREAKDOWN"]

@@ -1,0 +1,540 @@
+// The C ABI of libmgeig (declared in include/mgeig.h).  Every entry point
+// catches the library's internal errors and returns a status code.
+#include <chrono>
+#include <cstring>
+
+#include "internal.h"
+
+using namespace mgeig;
+
+struct mgeig_ctx {
+    Ctx c;
+};
+
+namespace {
+
+template <typename F>
+int guarded(mgeig_ctx *ctx, F f) {
+    if (!ctx) return MGEIG_EINVAL;
+    try {
+        MG_CUDA(cudaSetDevice(ctx->c.device));
+        return f(ctx->c);
+    } catch (const Error &e) {
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        return MGEIG_ENOMEM;
+    }
+}
+
+bool divides_all(const int *blk, const int *dims) {
+    for (int mu = 0; mu < 4; ++mu)
+        if (blk[mu] < 1 || dims[mu] % blk[mu]) return false;
+    return true;
+}
+
+int validate(const Ctx &c, const mgeig_params &p) {
+    for (int mu = 0; mu < 4; ++mu)
+        if (p.bc[mu] != 1 && p.bc[mu] != -1) return MGEIG_EINVAL;
+    if (!divides_all(p.agg, c.dims) || !divides_all(p.sap_block, c.dims)) return MGEIG_EINVAL;
+    int avol = 1, bvol = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        const int nb = c.dims[mu] / p.sap_block[mu];
+        if (nb < 2 || nb % 2) return MGEIG_EINVAL;
+        avol *= p.agg[mu];
+        bvol *= p.sap_block[mu];
+    }
+    if (avol > 1024 || bvol > 1024) return MGEIG_EINVAL;
+    if (p.n_tv < 2 || p.n_tv > 24 || 6 * avol < p.n_tv) return MGEIG_EINVAL;
+    if (p.sap_cycles < 0 || p.sap_mr_iters < 1 || p.smooth_steps < 0 || p.gmres_smooth_k < 1) return MGEIG_EINVAL;
+    if (p.setup_smooth < 0 || p.setup_iters < 0) return MGEIG_EINVAL;
+    if (p.outer_restart < 1 || p.outer_restart > 100 || p.outer_maxiter < 1) return MGEIG_EINVAL;
+    if (p.coarse_restart < 1 || p.coarse_restart > 100 || p.coarse_maxiter < 1) return MGEIG_EINVAL;
+    if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
+    if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
+    if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES) return MGEIG_EINVAL;
+    if (p.max_sweeps < 1 || p.n_guard < -1) return MGEIG_EINVAL;
+    return MGEIG_OK;
+}
+
+size_t spinor_bytes(const Ctx &c) { return c.fine_ncpx() * 16; }
+
+// host (caller) spinors -> internal FP64 device layout at dst
+void host_to_internal(Ctx &c, const double *host, void *dst) {
+    MG_CUDA(cudaMemcpyAsync(c.staging.p, host, spinor_bytes(c), cudaMemcpyHostToDevice, c.stream));
+    pack_spinor_f64(c, c.staging.as<double>(), dst, 1);
+}
+
+void internal_to_host(Ctx &c, const void *src, double *host) {
+    unpack_spinor_f64(c, src, c.staging.as<double>(), 1);
+    MG_CUDA(cudaMemcpyAsync(host, c.staging.p, spinor_bytes(c), cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+void mgeig_default_params(mgeig_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->m0 = 0.0;
+    p->csw = 1.0;
+    for (int mu = 0; mu < 4; ++mu) { p->bc[mu] = 1; p->agg[mu] = 4; p->sap_block[mu] = 4; }
+    p->n_tv = 20;
+    p->sap_cycles = 3;
+    p->sap_mr_iters = 4;
+    p->smooth_steps = 2;
+    p->gmres_smooth_k = 8;
+    p->setup_smooth = 3;
+    p->setup_iters = 6;
+    p->outer_restart = 20;
+    p->outer_maxiter = 200;
+    p->coarse_restart = 30;
+    p->coarse_maxiter = 300;
+    p->coarse_tol = 5e-2;
+    p->solve_tol = 1e-2;
+    p->precision = MGEIG_MIXED;
+    p->smoother = MGEIG_SAP;
+    p->max_sweeps = 50;
+    p->n_guard = -1;
+}
+
+int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
+    if (!out || !dims) return MGEIG_EINVAL;
+    *out = nullptr;
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2) return MGEIG_EINVAL;
+        V *= dims[mu];
+    }
+    if (V >= (1LL << 31) / 12) return MGEIG_EINVAL;
+    mgeig_ctx *ctx = new (std::nothrow) mgeig_ctx();
+    if (!ctx) return MGEIG_ENOMEM;
+    Ctx &c = ctx->c;
+    c.device = device;
+    int stride = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        c.dims[mu] = dims[mu];
+        c.g.L[mu] = dims[mu];
+        c.g.stride[mu] = stride;
+        stride *= dims[mu];
+        c.g.bc[mu] = 1;
+    }
+    c.g.V = (int)V;
+    mgeig_default_params(&c.prm);
+    int rc = guarded(ctx, [&](Ctx &c) {
+        MG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        c.timer.stream = c.stream;
+        c.U64.alloc((size_t)V * 4 * 9 * 16);
+        c.U32.alloc((size_t)V * 4 * 3 * 16);
+        c.clov64.alloc((size_t)V * 36 * 16);
+        c.clov32.alloc((size_t)V * 18 * 16);
+        c.staging.alloc((size_t)V * 4 * 9 * 16);   // largest host-layout transfer: the gauge field
+        ensure_reduction(c, 64);
+        return MGEIG_OK;
+    });
+    if (rc != MGEIG_OK) {
+        mgeig_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return MGEIG_OK;
+}
+
+void mgeig_destroy(mgeig_ctx *ctx) {
+    if (!ctx) return;
+    Ctx &c = ctx->c;
+    cudaSetDevice(c.device);
+    if (c.stream) cudaStreamSynchronize(c.stream);
+    try { c.timer.reset(); } catch (...) {}
+    mg_free(c);
+    c.U64.free(); c.U32.free(); c.clov64.free(); c.clov32.free(); c.staging.free();
+    c.red_partial.free(); c.red_out.free(); c.Dc.free();
+    for (auto &b : c.user_bufs) b.free();
+    if (c.pinned) cudaFreeHost(c.pinned);
+    if (c.stream) cudaStreamDestroy(c.stream);
+    delete ctx;
+}
+
+int mgeig_set_params(mgeig_ctx *ctx, const mgeig_params *p) {
+    if (!ctx || !p) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        int rc = validate(c, *p);
+        if (rc != MGEIG_OK) return rc;
+        sync(c);
+        mg_free(c);
+        c.prm = *p;
+        for (int mu = 0; mu < 4; ++mu) {
+            c.g.bc[mu] = p->bc[mu];
+            c.cdims[mu] = c.dims[mu] / p->agg[mu];
+        }
+        c.nagg = c.cdims[0] * c.cdims[1] * c.cdims[2] * c.cdims[3];
+        c.agg_vol = p->agg[0] * p->agg[1] * p->agg[2] * p->agg[3];
+        c.sap_vol = p->sap_block[0] * p->sap_block[1] * p->sap_block[2] * p->sap_block[3];
+        c.sap_nblk = (int)(c.g.V / c.sap_vol);
+        c.have_setup = false;
+        if (c.have_gauge) build_clover(c);
+        mg_alloc(c);
+        sync(c);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_load_gauge(mgeig_ctx *ctx, const double *U) {
+    if (!ctx || !U) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        MG_CUDA(cudaMemcpyAsync(c.staging.p, U, (size_t)c.g.V * 4 * 9 * 16, cudaMemcpyHostToDevice, c.stream));
+        pack_gauge(c, c.staging.as<double>());
+        build_clover(c);
+        c.have_gauge = true;
+        c.have_setup = false;
+        sync(c);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_load_gauge_dev(mgeig_ctx *ctx, const void *U_dev) {
+    if (!ctx || !U_dev) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        pack_gauge(c, static_cast<const double *>(U_dev));
+        build_clover(c);
+        c.have_gauge = true;
+        c.have_setup = false;
+        sync(c);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_get_clover(mgeig_ctx *ctx, double *A) {
+    if (!ctx || !A) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_gauge) return MGEIG_ENOTSETUP;
+        TmpBuf tmp;
+        tmp.alloc((size_t)c.g.V * 72 * 16);
+        unpack_clover(c, tmp.as<double>());
+        MG_CUDA(cudaMemcpyAsync(A, tmp.p, (size_t)c.g.V * 72 * 16, cudaMemcpyDeviceToHost, c.stream));
+        sync(c);
+        tmp.free();
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_alloc_dev(mgeig_ctx *ctx, size_t bytes, void **ptr) {
+    if (!ctx || !ptr) return MGEIG_EINVAL;
+    *ptr = nullptr;
+    return guarded(ctx, [&](Ctx &c) {
+        DevBuf b;
+        b.alloc(bytes);
+        c.user_bufs.push_back(b);
+        *ptr = b.p;
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_pack_spinors(mgeig_ctx *ctx, int prec, const double *host, void *dev, int n_fields) {
+    if (!ctx || !host || !dev || n_fields < 1) return MGEIG_EINVAL;
+    if (prec != MGEIG_PREC_F64 && prec != MGEIG_PREC_F32) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        TmpBuf t;
+        if (prec == MGEIG_PREC_F32) t.alloc(spinor_bytes(c));
+        for (int f = 0; f < n_fields; ++f) {
+            const double *h = host + (size_t)f * c.fine_ncpx() * 2;
+            if (prec == MGEIG_PREC_F64) {
+                host_to_internal(c, h, static_cast<char *>(dev) + (size_t)f * spinor_bytes(c));
+            } else {
+                host_to_internal(c, h, t.p);
+                convert_f64_to_f32(c, t.p, static_cast<char *>(dev) + (size_t)f * spinor_bytes(c) / 2, c.fine_ncpx());
+            }
+        }
+        sync(c);
+        t.free();
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_unpack_spinors(mgeig_ctx *ctx, int prec, const void *dev, double *host, int n_fields) {
+    if (!ctx || !host || !dev || n_fields < 1) return MGEIG_EINVAL;
+    if (prec != MGEIG_PREC_F64 && prec != MGEIG_PREC_F32) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        TmpBuf t;
+        if (prec == MGEIG_PREC_F32) t.alloc(spinor_bytes(c));
+        for (int f = 0; f < n_fields; ++f) {
+            double *h = host + (size_t)f * c.fine_ncpx() * 2;
+            if (prec == MGEIG_PREC_F64) {
+                internal_to_host(c, static_cast<const char *>(dev) + (size_t)f * spinor_bytes(c), h);
+            } else {
+                convert_f32_to_f64(c, static_cast<const char *>(dev) + (size_t)f * spinor_bytes(c) / 2, t.p, c.fine_ncpx());
+                internal_to_host(c, t.p, h);
+            }
+        }
+        return MGEIG_OK;
+    });
+}
+
+static int check_op(int op, int prec) {
+    if (op != MGEIG_OP_Q && op != MGEIG_OP_D) return MGEIG_EINVAL;
+    if (prec != MGEIG_PREC_F64 && prec != MGEIG_PREC_F32) return MGEIG_EINVAL;
+    return MGEIG_OK;
+}
+
+int mgeig_apply(mgeig_ctx *ctx, double sigma, int op, int prec, const double *x, double *y, int nrhs) {
+    if (!ctx || !x || !y || nrhs < 1) return MGEIG_EINVAL;
+    if (check_op(op, prec) != MGEIG_OK) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_gauge) return MGEIG_ENOTSETUP;
+        const int mode = op == MGEIG_OP_Q ? MODE_QSIGMA : MODE_DSIGMA;
+        TmpBuf a, b, a32, b32;
+        a.alloc(spinor_bytes(c));
+        b.alloc(spinor_bytes(c));
+        if (prec == MGEIG_PREC_F32) { a32.alloc(spinor_bytes(c) / 2); b32.alloc(spinor_bytes(c) / 2); }
+        for (int r = 0; r < nrhs; ++r) {
+            const size_t off = (size_t)r * c.fine_ncpx() * 2;
+            host_to_internal(c, x + off, a.p);
+            if (prec == MGEIG_PREC_F64) {
+                apply_fine<double>(c, mode, sigma, a.p, b.p);
+            } else {
+                convert_f64_to_f32(c, a.p, a32.p, c.fine_ncpx());
+                apply_fine<float>(c, mode, sigma, a32.p, b32.p);
+                convert_f32_to_f64(c, b32.p, b.p, c.fine_ncpx());
+            }
+            internal_to_host(c, b.p, y + off);
+        }
+        a.free(); b.free(); a32.free(); b32.free();
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_apply_dev(mgeig_ctx *ctx, double sigma, int op, int prec, const void *x, void *y) {
+    if (!ctx || !x || !y) return MGEIG_EINVAL;
+    if (check_op(op, prec) != MGEIG_OK) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_gauge) return MGEIG_ENOTSETUP;
+        const int mode = op == MGEIG_OP_Q ? MODE_QSIGMA : MODE_DSIGMA;
+        if (prec == MGEIG_PREC_F64) apply_fine<double>(c, mode, sigma, x, y);
+        else apply_fine<float>(c, mode, sigma, x, y);
+        return MGEIG_OK;
+    });
+}
+
+static int need_setup(Ctx &c) {
+    if (!c.have_gauge) return MGEIG_ENOTSETUP;
+    if (!c.work) return MGEIG_ENOTSETUP;
+    return MGEIG_OK;
+}
+
+static void begin_stats(Ctx &c) { std::memset(&c.st, 0, sizeof(c.st)); }
+static void end_stats(Ctx &c, mgeig_stats *out, std::chrono::steady_clock::time_point t0) {
+    coarse_iters_take(c);
+    c.st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (out) *out = c.st;
+}
+
+int mgeig_setup(mgeig_ctx *ctx, uint64_t seed, mgeig_stats *stats) {
+    return guarded(ctx, [&](Ctx &c) {
+        int rc = need_setup(c);
+        if (rc) return rc;
+        auto t0 = std::chrono::steady_clock::now();
+        begin_stats(c);
+        setup(c, seed);
+        end_stats(c, stats, t0);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_set_test_vectors(mgeig_ctx *ctx, const double *W) {
+    if (!W) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        int rc = need_setup(c);
+        if (rc) return rc;
+        for (int j = 0; j < c.prm.n_tv; ++j) host_to_internal(c, W + (size_t)j * c.fine_ncpx() * 2, mg_test_vector(c, j));
+        mg_rebuild(c);
+        sync(c);
+        c.have_setup = true;
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_get_test_vectors(mgeig_ctx *ctx, double *W) {
+    if (!W) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        for (int j = 0; j < c.prm.n_tv; ++j) internal_to_host(c, mg_test_vector(c, j), W + (size_t)j * c.fine_ncpx() * 2);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_get_interp(mgeig_ctx *ctx, double *P) {
+    if (!P) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        const int ntv = c.prm.n_tv;
+        std::vector<TmpBuf> tmp(ntv);
+        std::vector<void *> ptr(ntv);
+        for (int j = 0; j < ntv; ++j) { tmp[j].alloc(spinor_bytes(c)); ptr[j] = tmp[j].p; }
+        interp_f64(c, ptr.data());
+        for (int j = 0; j < ntv; ++j) internal_to_host(c, ptr[j], P + (size_t)j * c.fine_ncpx() * 2);
+        for (auto &t : tmp) t.free();
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_get_coarse_op(mgeig_ctx *ctx, double *Dc) {
+    if (!Dc) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        const int n2 = 2 * c.prm.n_tv;
+        const size_t bytes = (size_t)9 * c.nagg * n2 * n2 * 16;
+        TmpBuf t;
+        t.alloc(bytes);
+        coarse_op_f64(c, t.p);
+        MG_CUDA(cudaMemcpyAsync(Dc, t.p, bytes, cudaMemcpyDeviceToHost, c.stream));
+        sync(c);
+        t.free();
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_restrict(mgeig_ctx *ctx, const double *r, double *rc) {
+    if (!r || !rc) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        TmpBuf a, b;
+        a.alloc(spinor_bytes(c));
+        b.alloc(c.coarse_ncpx() * 16);
+        host_to_internal(c, r, a.p);
+        restrict_f64(c, a.p, b.p);
+        MG_CUDA(cudaMemcpyAsync(rc, b.p, c.coarse_ncpx() * 16, cudaMemcpyDeviceToHost, c.stream));
+        sync(c);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_prolong(mgeig_ctx *ctx, const double *ec, double *e) {
+    if (!ec || !e) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        TmpBuf a, b;
+        a.alloc(c.coarse_ncpx() * 16);
+        b.alloc(spinor_bytes(c));
+        MG_CUDA(cudaMemcpyAsync(a.p, ec, c.coarse_ncpx() * 16, cudaMemcpyHostToDevice, c.stream));
+        prolong_f64(c, a.p, b.p);
+        internal_to_host(c, b.p, e);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_coarse_apply(mgeig_ctx *ctx, double sigma, const double *xc, double *yc) {
+    if (!xc || !yc) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        TmpBuf a, b;
+        a.alloc(c.coarse_ncpx() * 16);
+        b.alloc(c.coarse_ncpx() * 16);
+        MG_CUDA(cudaMemcpyAsync(a.p, xc, c.coarse_ncpx() * 16, cudaMemcpyHostToDevice, c.stream));
+        coarse_apply_f64(c, sigma, a.p, b.p);
+        MG_CUDA(cudaMemcpyAsync(yc, b.p, c.coarse_ncpx() * 16, cudaMemcpyDeviceToHost, c.stream));
+        sync(c);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_sap(mgeig_ctx *ctx, double sigma, const double *b, double *z, int cycles) {
+    if (!b || !z || cycles < 0) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_gauge || !c.work) return MGEIG_ENOTSETUP;
+        TmpBuf a, bb;
+        a.alloc(spinor_bytes(c));
+        bb.alloc(spinor_bytes(c));
+        host_to_internal(c, b, a.p);
+        host_to_internal(c, z, bb.p);
+        sap_smooth_f64(c, sigma, a.p, bb.p, cycles);
+        internal_to_host(c, bb.p, z);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_mg_cycle(mgeig_ctx *ctx, double sigma, const double *r, double *z) {
+    if (!r || !z) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        TmpBuf a, b;
+        a.alloc(spinor_bytes(c));
+        b.alloc(spinor_bytes(c));
+        host_to_internal(c, r, a.p);
+        mg_cycle_host(c, sigma, a.as<double>(), b.as<double>());
+        internal_to_host(c, b.p, z);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_solve(mgeig_ctx *ctx, double sigma, const double *b, double *x, double tol, mgeig_stats *stats) {
+    if (!b || !x || !(tol > 0)) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        auto t0 = std::chrono::steady_clock::now();
+        begin_stats(c);
+        TmpBuf a, bb;
+        a.alloc(spinor_bytes(c));
+        bb.alloc(spinor_bytes(c));
+        host_to_internal(c, b, a.p);
+        int rc = fgmres_solve(c, sigma, a.p, bb.p, tol);
+        internal_to_host(c, bb.p, x);
+        end_stats(c, stats, t0);
+        return rc;
+    });
+}
+
+int mgeig_eigensolve(mgeig_ctx *ctx, int n_eig, double tol, double *evals, double *evecs, double *resid,
+                     mgeig_stats *stats) {
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        if (n_eig < 1 || n_eig > c.prm.n_tv || !(tol > 0)) return MGEIG_EINVAL;
+        auto t0 = std::chrono::steady_clock::now();
+        begin_stats(c);
+        int rc = eigensolve(c, n_eig, tol, evals, evecs, resid);
+        sync(c);
+        end_stats(c, stats, t0);
+        return rc;
+    });
+}
+
+int mgeig_set_timing(mgeig_ctx *ctx, int on) {
+    return guarded(ctx, [&](Ctx &c) {
+        c.timer.reset();
+        c.timer.on = on != 0;
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms, double *bytes, const char **names) {
+    static const char *kNames[K_NCLASS] = {"stencil_f64", "stencil_f32", "sap_f64",      "sap_f32",
+                                           "restrict",    "prolong",     "coarse_apply", "coarse_build",
+                                           "interp_build", "blas_f64",   "blas_low",     "other",
+                                           "coarse_gmres"};
+    return guarded(ctx, [&](Ctx &c) {
+        c.timer.flush();
+        for (int k = 0; k < n && k < K_NCLASS; ++k) {
+            if (launches) launches[k] = c.timer.launches[k];
+            if (ms) ms[k] = c.timer.ms[k];
+            if (bytes) bytes[k] = c.timer.total_bytes[k];
+            if (names) names[k] = kNames[k];
+        }
+        return (int)K_NCLASS;
+    });
+}
+
+const char *mgeig_strerror(int status) {
+    switch (status) {
+        case MGEIG_OK: return "ok";
+        case MGEIG_EINVAL: return "invalid argument";
+        case MGEIG_ENOTSETUP: return "gauge field or multigrid setup missing";
+        case MGEIG_ECUDA: return "CUDA runtime error";
+        case MGEIG_ENOCONV: return "iteration cap reached before convergence";
+        case MGEIG_EBREAKDOWN: return "numerical breakdown (NaN/Inf or zero vector)";
+        case MGEIG_ENOMEM: return "device memory allocation failed";
+        case MGEIG_ETIMEOUT: return "a bounded device-side wait expired";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+// BLAS-1 on flat complex arrays (fine spinors of one precision share one
+// layout, so element-wise operations ignore it; coarse vectors are flat).
+//
+// Reductions are deterministic two-pass trees: a fixed grid of 256-thread
+// blocks accumulates grid-stride partial sums (per thread in the array's own
+// precision, then in FP64 across the block with warp shuffles), writes one
+// partial per block, and a second kernel adds the partials in a fixed order.
+// Inner products of up to 8 vectors against one vector share one read of that
+// vector (the Arnoldi / Gram-Schmidt steps of GMRES, FGMRES and Algorithm 1).
+#include "internal.h"
+
+namespace mgeig {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAXBLOCKS = 1024;
+constexpr int CHUNK = 8;
+
+template <typename R> struct V2;
+template <> struct V2<double> { typedef double2 T; };
+template <> struct V2<float> { typedef float2 T; };
+
+struct PtrPack { const void *p[CHUNK]; };
+
+static int red_grid(size_t n) {
+    size_t b = (n + RED_THREADS * 4 - 1) / (RED_THREADS * 4);
+    if (b < 1) b = 1;
+    if (b > RED_MAXBLOCKS) b = RED_MAXBLOCKS;
+    return (int)b;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-reduce `cnt` complex values held by every thread; thread 0 writes them
+template <int MAXV>
+__device__ __forceinline__ void block_reduce_store(double (&re)[MAXV], double (&im)[MAXV], int cnt, double2 *out,
+                                                   size_t out_stride) {
+    __shared__ double sh[RED_THREADS / 32][2 * MAXV];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+        if (k < cnt) {
+            double a = warp_sum(re[k]), b = warp_sum(im[k]);
+            if (lane == 0) { sh[w][2 * k] = a; sh[w][2 * k + 1] = b; }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+        double a = 0, b = 0;
+        for (int i = 0; i < RED_THREADS / 32; ++i) { a += sh[i][2 * threadIdx.x]; b += sh[i][2 * threadIdx.x + 1]; }
+        out[(size_t)threadIdx.x * out_stride + blockIdx.x] = make_double2(a, b);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) multidot_kernel(PtrPack X, int k, const void *__restrict__ yv, size_t n,
+                                                               double2 *__restrict__ partial, size_t pstride) {
+    typedef typename V2<R>::T T;
+    const T *y = static_cast<const T *>(yv);
+    R ar[CHUNK], ai[CHUNK];
+#pragma unroll
+    for (int j = 0; j < CHUNK; ++j) { ar[j] = 0; ai[j] = 0; }
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T b = y[i];
+#pragma unroll
+        for (int j = 0; j < CHUNK; ++j) {
+            if (j < k) {
+                T a = static_cast<const T *>(X.p[j])[i];
+                ar[j] = fma(a.x, b.x, ar[j]); ar[j] = fma(a.y, b.y, ar[j]);
+                ai[j] = fma(a.x, b.y, ai[j]); ai[j] = fma(-a.y, b.x, ai[j]);
+            }
+        }
+    }
+    double re[CHUNK], im[CHUNK];
+#pragma unroll
+    for (int j = 0; j < CHUNK; ++j) { re[j] = ar[j]; im[j] = ai[j]; }
+    block_reduce_store<CHUNK>(re, im, k, partial, pstride);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) norm2_kernel(const void *__restrict__ xv, size_t n,
+                                                            double2 *__restrict__ partial) {
+    typedef typename V2<R>::T T;
+    const T *x = static_cast<const T *>(xv);
+    R acc = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T a = x[i];
+        acc = fma(a.x, a.x, acc); acc = fma(a.y, a.y, acc);
+    }
+    double re[1] = {(double)acc}, im[1] = {0.0};
+    block_reduce_store<1>(re, im, 1, partial, 1);
+}
+
+__global__ void resid_norm2_kernel(const double2 *__restrict__ qv, const double2 *__restrict__ v,
+                                   const double2 *__restrict__ lam, size_t n, double2 *__restrict__ partial) {
+    const double l = lam[0].x;
+    double acc = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 a = qv[i], b = v[i];
+        double rx = fma(-l, b.x, a.x), ry = fma(-l, b.y, a.y);
+        acc = fma(rx, rx, acc); acc = fma(ry, ry, acc);
+    }
+    double re[1] = {acc}, im[1] = {0.0};
+    block_reduce_store<1>(re, im, 1, partial, 1);
+}
+
+// out[j] = sum of partial[j][0..nb)
+__global__ void finalize_kernel(const double2 *__restrict__ partial, size_t pstride, int nb, double2 *__restrict__ out) {
+    const int j = blockIdx.x;
+    double a = 0, b = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) { double2 t = partial[(size_t)j * pstride + i]; a += t.x; b += t.y; }
+    a = warp_sum(a); b = warp_sum(b);
+    __shared__ double sh[2][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][w] = a; sh[1][w] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { x += sh[0][i]; y += sh[1][i]; }
+        out[j] = make_double2(x, y);
+    }
+}
+
+static double2 *partial_ptr(Ctx &c) { return c.red_partial.as<double2>(); }
+
+template <typename R>
+void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n, cpx<double> *d_out) {
+    const int nb = red_grid(n);
+    const size_t pstride = RED_MAXBLOCKS;
+    TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)(k + 1) * n * 2 * sizeof(R));
+    for (int j0 = 0; j0 < k; j0 += CHUNK) {
+        PtrPack pk{};
+        const int kk = k - j0 < CHUNK ? k - j0 : CHUNK;
+        for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
+        multidot_kernel<R><<<nb, RED_THREADS, 0, c.stream>>>(pk, kk, y, n, partial_ptr(c) + (size_t)j0 * pstride, pstride);
+        MG_CHECK_LAUNCH();
+    }
+    finalize_kernel<<<k, 128, 0, c.stream>>>(partial_ptr(c), pstride, nb, reinterpret_cast<double2 *>(d_out));
+    MG_CHECK_LAUNCH();
+}
+
+template <typename R>
+void blas_norm2(Ctx &c, const void *x, size_t n, cpx<double> *d_out) {
+    const int nb = red_grid(n);
+    TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)n * 2 * sizeof(R));
+    norm2_kernel<R><<<nb, RED_THREADS, 0, c.stream>>>(x, n, partial_ptr(c));
+    MG_CHECK_LAUNCH();
+    finalize_kernel<<<1, 128, 0, c.stream>>>(partial_ptr(c), RED_MAXBLOCKS, nb, reinterpret_cast<double2 *>(d_out));
+    MG_CHECK_LAUNCH();
+}
+
+void blas_resid_norm2(Ctx &c, const void *qv, const void *v, const cpx<double> *d_lambda, size_t n, cpx<double> *d_out) {
+    const int nb = red_grid(n);
+    TimeScope ts(c.timer, K_BLAS_F64, (double)n * 32);
+    resid_norm2_kernel<<<nb, RED_THREADS, 0, c.stream>>>(static_cast<const double2 *>(qv), static_cast<const double2 *>(v),
+                                                         reinterpret_cast<const double2 *>(d_lambda), n, partial_ptr(c));
+    MG_CHECK_LAUNCH();
+    finalize_kernel<<<1, 128, 0, c.stream>>>(partial_ptr(c), RED_MAXBLOCKS, nb, reinterpret_cast<double2 *>(d_out));
+    MG_CHECK_LAUNCH();
+}
+
+// y += sign * sum_j coef[j] X_j
+template <typename R>
+__global__ void multi_axpy_kernel(void *__restrict__ yv, PtrPack X, int k, const double2 *__restrict__ coef, double sign,
+                                  size_t n) {
+    typedef typename V2<R>::T T;
+    T *y = static_cast<T *>(yv);
+    R cr[CHUNK], ci[CHUNK];
+#pragma unroll
+    for (int j = 0; j < CHUNK; ++j) {
+        if (j < k) { double2 t = coef[j]; cr[j] = (R)(sign * t.x); ci[j] = (R)(sign * t.y); }
+        else { cr[j] = 0; ci[j] = 0; }
+    }
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T acc = y[i];
+#pragma unroll
+        for (int j = 0; j < CHUNK; ++j) {
+            if (j < k) {
+                T a = static_cast<const T *>(X.p[j])[i];
+                acc.x = fma(cr[j], a.x, acc.x); acc.x = fma(-ci[j], a.y, acc.x);
+                acc.y = fma(cr[j], a.y, acc.y); acc.y = fma(ci[j], a.x, acc.y);
+            }
+        }
+        y[i] = acc;
+    }
+}
+
+static int ew_grid(size_t n) {
+    size_t b = (n + 255) / 256;
+    const size_t cap = 152 * 16;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <typename R>
+void blas_multi_axpy(Ctx &c, void *y, const void *const *X, int k, const cpx<double> *d_coef, double sign, size_t n) {
+    TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)(k + 2) * n * 2 * sizeof(R));
+    for (int j0 = 0; j0 < k; j0 += CHUNK) {
+        PtrPack pk{};
+        const int kk = k - j0 < CHUNK ? k - j0 : CHUNK;
+        for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
+        multi_axpy_kernel<R><<<ew_grid(n), 256, 0, c.stream>>>(y, pk, kk, reinterpret_cast<const double2 *>(d_coef + j0),
+                                                               sign, n);
+        MG_CHECK_LAUNCH();
+    }
+}
+
+template <typename R>
+__global__ void axpy_kernel(double ar, double ai, const void *__restrict__ xv, void *__restrict__ yv, size_t n) {
+    typedef typename V2<R>::T T;
+    const T *x = static_cast<const T *>(xv);
+    T *y = static_cast<T *>(yv);
+    const R a = (R)ar, b = (R)ai;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T u = x[i], v = y[i];
+        v.x = fma(a, u.x, v.x); v.x = fma(-b, u.y, v.x);
+        v.y = fma(a, u.y, v.y); v.y = fma(b, u.x, v.y);
+        y[i] = v;
+    }
+}
+
+template <typename R>
+__global__ void scale_kernel(double ar, double ai, void *__restrict__ xv, size_t n) {
+    typedef typename V2<R>::T T;
+    T *x = static_cast<T *>(xv);
+    const R a = (R)ar, b = (R)ai;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T u = x[i];
+        T v;
+        v.x = a * u.x - b * u.y;
+        v.y = a * u.y + b * u.x;
+        x[i] = v;
+    }
+}
+
+template <typename R>
+void blas_axpy(Ctx &c, cpx<double> a, const void *x, void *y, size_t n) {
+    TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, 3.0 * n * 2 * sizeof(R));
+    axpy_kernel<R><<<ew_grid(n), 256, 0, c.stream>>>(a.re, a.im, x, y, n);
+    MG_CHECK_LAUNCH();
+}
+
+template <typename R>
+void blas_scale(Ctx &c, cpx<double> a, void *x, size_t n) {
+    TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, 2.0 * n * 2 * sizeof(R));
+    scale_kernel<R><<<ew_grid(n), 256, 0, c.stream>>>(a.re, a.im, x, n);
+    MG_CHECK_LAUNCH();
+}
+
+template <typename R>
+void blas_copy(Ctx &c, const void *x, void *y, size_t n) {
+    MG_CUDA(cudaMemcpyAsync(y, x, n * 2 * sizeof(R), cudaMemcpyDeviceToDevice, c.stream));
+}
+
+template <typename R>
+void blas_zero(Ctx &c, void *x, size_t n) {
+    MG_CUDA(cudaMemsetAsync(x, 0, n * 2 * sizeof(R), c.stream));
+}
+
+// y (FP64 fine layout) += a * x (fine layout of precision R)
+template <typename R>
+__global__ void axpy_to_f64_fine_kernel(int V, double ar, double ai, const void *__restrict__ x, double2 *__restrict__ y) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    cpx<R> v[12];
+    Spinor<R>::load(x, V, s, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2 t = y[(size_t)k * V + s];
+        double xr = v[k].re, xi = v[k].im;
+        t.x = fma(ar, xr, t.x); t.x = fma(-ai, xi, t.x);
+        t.y = fma(ar, xi, t.y); t.y = fma(ai, xr, t.y);
+        y[(size_t)k * V + s] = t;
+    }
+}
+
+template <typename R>
+void blas_axpy_to_f64(Ctx &c, cpx<double> a, const void *x, void *y64, size_t n) {
+    const int V = (int)(n / 12);
+    TimeScope ts(c.timer, K_BLAS_F64, (double)n * (2 * sizeof(R) + 32));
+    axpy_to_f64_fine_kernel<R><<<grid_for(V, 256), 256, 0, c.stream>>>(V, a.re, a.im, x, static_cast<double2 *>(y64));
+    MG_CHECK_LAUNCH();
+}
+
+#define INST(R)                                                                                             \
+    template void blas_multidot<R>(Ctx &, const void *const *, int, const void *, size_t, cpx<double> *);    \
+    template void blas_multi_axpy<R>(Ctx &, void *, const void *const *, int, const cpx<double> *, double, size_t); \
+    template void blas_norm2<R>(Ctx &, const void *, size_t, cpx<double> *);                                     \
+    template void blas_axpy<R>(Ctx &, cpx<double>, const void *, void *, size_t);                          \
+    template void blas_scale<R>(Ctx &, cpx<double>, void *, size_t);                                       \
+    template void blas_copy<R>(Ctx &, const void *, void *, size_t);                                       \
+    template void blas_zero<R>(Ctx &, void *, size_t);                                                     \
+    template void blas_axpy_to_f64<R>(Ctx &, cpx<double>, const void *, void *, size_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace mgeig

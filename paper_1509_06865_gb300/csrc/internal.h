@@ -1,0 +1,202 @@
+// Host-side internals of libmgeig: the context, device buffers, launch wrappers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/mgeig.h"
+#include "common.cuh"
+
+namespace mgeig {
+
+// Status propagation: every CUDA runtime error becomes MGEIG_ECUDA, with the
+// message kept in the context for mgeig_strerror-style diagnostics on stderr.
+struct Error {
+    int code;
+};
+
+#define MG_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            fprintf(stderr, "libmgeig: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), \
+                    __FILE__, __LINE__);                                                   \
+            throw ::mgeig::Error{e_ == cudaErrorMemoryAllocation ? MGEIG_ENOMEM : MGEIG_ECUDA}; \
+        }                                                                                  \
+    } while (0)
+
+#define MG_CHECK_LAUNCH() MG_CUDA(cudaGetLastError())
+
+#define MG_REQUIRE(cond, code)           \
+    do {                                 \
+        if (!(cond)) throw ::mgeig::Error{code}; \
+    } while (0)
+
+// A device allocation owned by the context.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void alloc(size_t n);
+    void free();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+// A scoped device allocation, released when it goes out of scope.
+struct TmpBuf : DevBuf {
+    TmpBuf() = default;
+    TmpBuf(const TmpBuf &) = delete;
+    TmpBuf &operator=(const TmpBuf &) = delete;
+    ~TmpBuf() { free(); }
+};
+
+// Kernel classes with per-class CUDA event timing (off unless enabled).
+enum KernelClass {
+    K_STENCIL_F64 = 0, K_STENCIL_F32, K_SAP_F64, K_SAP_F32, K_RESTRICT, K_PROLONG,
+    K_COARSE_APPLY, K_COARSE_BUILD, K_PBUILD, K_BLAS_F64, K_BLAS_LOW, K_OTHER, K_COARSE_SOLVE, K_NCLASS
+};
+
+struct Timer {
+    bool on = false;
+    cudaStream_t stream = nullptr;
+    long long launches[K_NCLASS] = {};
+    double ms[K_NCLASS] = {};
+    double bytes[K_NCLASS] = {};        // algorithmic bytes of the last launch
+    double total_bytes[K_NCLASS] = {};  // algorithmic bytes summed over launches
+    std::vector<cudaEvent_t> pool;
+    struct Pending { int cls; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    size_t next = 0;
+    cudaEvent_t begin(int cls);
+    void end(int cls, cudaEvent_t a, double bytes);
+    void flush();
+    void reset();
+    ~Timer();
+};
+
+// RAII bracket around one launch of a kernel class.
+struct TimeScope {
+    Timer &t; int cls; double bytes; cudaEvent_t a = nullptr;
+    TimeScope(Timer &t_, int cls_, double bytes_) : t(t_), cls(cls_), bytes(bytes_) {
+        if (t.on) a = t.begin(cls);
+        t.launches[cls] += 1;
+        t.total_bytes[cls] += bytes_;
+    }
+    ~TimeScope() { if (t.on) t.end(cls, a, bytes); else t.bytes[cls] = bytes; }
+};
+
+struct Ctx;
+
+// ----- fine operator (fine_op.cu) -----
+void pack_gauge(Ctx &c, const double *dev_host_layout);
+void build_clover(Ctx &c);
+void unpack_clover(Ctx &c, double *dev_out);
+template <typename R> void apply_fine(Ctx &c, int mode, double sigma, const void *x, void *y);
+// x in FP32 internal layout, y FP64: y = op(x) in FP64 arithmetic
+void apply_fine_f64_from_f32(Ctx &c, int mode, double sigma, const void *x32, void *y64);
+void pack_spinor_f64(Ctx &c, const double *host_layout_dev, void *out, int n);
+void unpack_spinor_f64(Ctx &c, const void *in, double *host_layout_dev, int n);
+void convert_f64_to_f32(Ctx &c, const void *in64, void *out32, size_t ncomplex);
+void convert_f32_to_f64(Ctx &c, const void *in32, void *out64, size_t ncomplex);
+void random_spinors(Ctx &c, uint64_t seed, void *out64, int n);
+
+// ----- BLAS-1 on flat complex arrays (blas.cu) -----
+// Results of reductions land in device memory (cpx<double>); *_host variants sync.
+template <typename R> void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n, cpx<double> *d_out);
+template <typename R> void blas_multi_axpy(Ctx &c, void *y, const void *const *X, int k, const cpx<double> *d_coef, double sign, size_t n);
+template <typename R> void blas_norm2(Ctx &c, const void *x, size_t n, cpx<double> *d_out);
+template <typename R> void blas_axpy(Ctx &c, cpx<double> a, const void *x, void *y, size_t n);
+template <typename R> void blas_scale(Ctx &c, cpx<double> a, void *x, size_t n);
+template <typename R> void blas_copy(Ctx &c, const void *x, void *y, size_t n);
+template <typename R> void blas_zero(Ctx &c, void *x, size_t n);
+// y (FP64) += a * x (R)
+template <typename R> void blas_axpy_to_f64(Ctx &c, cpx<double> a, const void *x, void *y64, size_t n);
+// y = x - lambda_dev[0] * v ; out = ||y||^2  (FP64; lambda on the device)
+void blas_resid_norm2(Ctx &c, const void *qv, const void *v, const cpx<double> *d_lambda, size_t n, cpx<double> *d_out);
+
+// ----- multigrid (mg.cu) -----
+template <typename R> void build_interp(Ctx &c, const void *const *W64, int ntv, void *const *P);
+template <typename R> void restrict_vec(Ctx &c, const void *const *P, const void *r, void *rc);
+template <typename R> void prolong_vec(Ctx &c, const void *const *P, const void *ec, void *e);
+template <typename R> void build_coarse(Ctx &c, const void *const *P, void *Dc);
+template <typename R> void coarse_apply(Ctx &c, const void *Dc, double sigma, const void *x, void *y);
+template <typename R> void sap_sweep(Ctx &c, int colour, double sigma, const void *rhs, bool rhs_gamma5, void *z);
+
+// ----- persistent coarse GMRES (coarse_gmres.cu) -----
+constexpr int COARSE_PERSISTENT_MAXM = 32;
+template <typename R>
+void coarse_gmres_persistent(Ctx &c, double sigma, const void *rc, void *ec, DevBuf &Vbuf, DevBuf &pbuf, void *state);
+
+// ----- the context -----
+struct Ctx {
+    int dims[4];
+    Geom g;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mgeig_params prm;
+    bool have_gauge = false;
+    bool have_setup = false;
+    Timer timer;
+
+    // fine fields
+    DevBuf U64, U32, clov64, clov32;
+    DevBuf staging;           // host-layout transfer buffer
+    std::vector<DevBuf> user_bufs;
+
+    // reduction scratch
+    DevBuf red_partial;       // per-block partial sums
+    DevBuf red_out;           // reduction results (cpx<double>)
+    size_t red_blocks = 0;
+    double *pinned = nullptr; // host mirror of red_out
+
+    // multigrid geometry
+    int cdims[4] = {0, 0, 0, 0};
+    int nagg = 0, agg_vol = 0;
+    int sap_nblk = 0, sap_vol = 0;
+
+    // test vectors (FP64) and interpolation / coarse operator in the level precision
+    std::vector<DevBuf> W;    // ntv FP64 fine vectors
+    std::vector<DevBuf> P;    // ntv vectors, R precision
+    DevBuf Dc;                // [9][nagg][2N][2N] (column-major blocks), R precision
+
+    size_t fine_ncpx() const { return (size_t)g.V * 12; }
+    size_t coarse_ncpx() const { return (size_t)nagg * 2 * prm.n_tv; }
+    bool mixed() const { return prm.precision == MGEIG_MIXED; }
+    size_t level_bytes() const { return mixed() ? sizeof(float) : sizeof(double); }
+
+    // host workspace counters
+    mgeig_stats st{};
+
+    // solver workspace (allocated lazily, see solver.cu)
+    struct Work;
+    Work *work = nullptr;
+};
+
+// ----- solvers (solver.cu) -----
+void ensure_reduction(Ctx &c, int max_vectors);
+void sync(Ctx &c);
+void read_reduction(Ctx &c, int n);   // copies n cpx<double> from red_out into pinned
+cpx<double> host_red(Ctx &c, int i);
+
+void mg_alloc(Ctx &c);
+void coarse_iters_take(Ctx &c);
+void mg_free(Ctx &c);
+void *mg_test_vector(Ctx &c, int j);
+void mg_rebuild(Ctx &c);   // P and coarse operator from c.W
+void setup(Ctx &c, uint64_t seed);
+void mg_cycle_host(Ctx &c, double sigma, const double *r_dev64_internal, double *z_dev64_internal);
+int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol);
+int eigensolve(Ctx &c, int n_eig, double tol, double *evals, double *evecs_host, double *resid);
+void sap_smooth_f64(Ctx &c, double sigma, const void *b64, void *z64, int cycles);
+void coarse_apply_f64(Ctx &c, double sigma, const void *x64, void *y64);
+void restrict_f64(Ctx &c, const void *r64, void *rc64);
+void prolong_f64(Ctx &c, const void *ec64, void *e64);
+void coarse_op_f64(Ctx &c, void *out64);
+void interp_f64(Ctx &c, void *const *out64);
+
+int grid_for(size_t n, int threads);
+
+}  // namespace mgeig

@@ -1,0 +1,862 @@
+// Host orchestration of the solvers (native C++ driving the kernels):
+//   GMRES(m) on either level, the two-grid cycle B (Eq. 2.3, mu = 0 pre- and
+//   nu post-smoothing steps), the FP64 flexible GMRES of every shifted solve
+//   (Sec. 2.2: double precision FGMRES preconditioned by single precision
+//   multigrid), the multigrid setup and the Rayleigh quotient iteration of
+//   Algorithm 1.
+//
+// Scalars of the Krylov methods (Hessenberg columns, norms) are reduced on the
+// device and read back once per Arnoldi step; the Givens rotations and the
+// small triangular solves run on the host.
+#include <chrono>
+#include <cmath>
+#include <algorithm>
+#include <numeric>
+
+#include "internal.h"
+
+namespace mgeig {
+
+// ---------------------------------------------------------------------------
+// device buffers, timer
+
+void DevBuf::alloc(size_t n) {
+    if (bytes >= n && p) return;
+    free();
+    if (n == 0) return;
+    MG_CUDA(cudaMalloc(&p, n));
+    bytes = n;
+}
+
+void DevBuf::free() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+cudaEvent_t Timer::begin(int) {
+    if (next + 2 > pool.size()) {
+        flush();
+        while (pool.size() < next + 2) {
+            cudaEvent_t e;
+            MG_CUDA(cudaEventCreate(&e));
+            pool.push_back(e);
+        }
+    }
+    cudaEvent_t a = pool[next++];
+    MG_CUDA(cudaEventRecord(a, stream));
+    return a;
+}
+
+void Timer::end(int cls, cudaEvent_t a, double b) {
+    cudaEvent_t e = pool[next++];
+    MG_CUDA(cudaEventRecord(e, stream));
+    pending.push_back({cls, a, e});
+    bytes[cls] = b;
+    if (pending.size() >= 1024) flush();
+}
+
+void Timer::flush() {
+    if (!pending.empty()) {
+        MG_CUDA(cudaEventSynchronize(pending.back().b));
+        for (auto &p : pending) {
+            float t = 0;
+            MG_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
+            ms[p.cls] += t;
+        }
+        pending.clear();
+    }
+    next = 0;
+}
+
+void Timer::reset() {
+    flush();
+    for (int k = 0; k < K_NCLASS; ++k) { launches[k] = 0; ms[k] = 0; total_bytes[k] = 0; }
+}
+
+Timer::~Timer() {
+    for (auto e : pool) cudaEventDestroy(e);
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+
+constexpr int RED_SLOTS = 512;       // cpx<double> results on the device
+// slots: Hessenberg passes H1, H2, norm HN, the persistent coarse solver's
+// state CGS (status word and iteration counter), uploads from UP on
+constexpr int H1 = 0, H2 = 128, HN = 256, CGS = 257, NFETCH = 258, UP = 300;
+
+void ensure_reduction(Ctx &c, int max_vectors) {
+    (void)max_vectors;
+    if (!c.red_partial.p) {
+        c.red_partial.alloc((size_t)64 * 1024 * sizeof(double2));
+        c.red_out.alloc(RED_SLOTS * sizeof(double2));
+        MG_CUDA(cudaMemset(c.red_out.p, 0, RED_SLOTS * sizeof(double2)));
+        MG_CUDA(cudaMallocHost(&c.pinned, 2 * RED_SLOTS * sizeof(double2)));
+    }
+}
+
+void sync(Ctx &c) { MG_CUDA(cudaStreamSynchronize(c.stream)); }
+
+static cpx<double> *dslot(Ctx &c, int i) { return c.red_out.as<cpx<double>>() + i; }
+static cpx<double> *hslot(Ctx &c, int i) { return reinterpret_cast<cpx<double> *>(c.pinned) + i; }
+static cpx<double> *upslot(Ctx &c, int i) { return reinterpret_cast<cpx<double> *>(c.pinned) + RED_SLOTS + i; }
+
+struct CoarseState { unsigned int count, gen; int status, iters; };
+
+// copy device slots [0, n) to the host mirror and wait; every fetch also
+// brings back the persistent coarse solver's state and raises its errors
+static void fetch(Ctx &c, int n) {
+    n = std::max(n, NFETCH);
+    MG_CUDA(cudaMemcpyAsync(c.pinned, c.red_out.p, n * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+    const CoarseState *cs = reinterpret_cast<const CoarseState *>(c.pinned + 2 * CGS);
+    if (cs->status != 0) {
+        const int code = cs->status == 1 ? MGEIG_ETIMEOUT : MGEIG_EBREAKDOWN;
+        MG_CUDA(cudaMemsetAsync(dslot(c, CGS), 0, sizeof(CoarseState), c.stream));
+        sync(c);
+        throw Error{code};
+    }
+}
+
+// upload host coefficients to device slots starting at UP
+static cpx<double> *upload(Ctx &c, const std::vector<cpx<double>> &v) {
+    MG_REQUIRE((int)v.size() <= RED_SLOTS - UP, MGEIG_EINVAL);
+    // the previous upload may still be read by an in-flight kernel
+    sync(c);
+    for (size_t i = 0; i < v.size(); ++i) *upslot(c, (int)i) = v[i];
+    MG_CUDA(cudaMemcpyAsync(dslot(c, UP), upslot(c, 0), v.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+    return dslot(c, UP);
+}
+
+static bool finite(cpx<double> z) { return std::isfinite(z.re) && std::isfinite(z.im); }
+
+// ---------------------------------------------------------------------------
+// workspace
+
+struct Ctx::Work {
+    int outer_m = 0, coarse_m = 0, smooth_k = 0, ntv = 0;
+    bool mixed = false;
+    DevBuf Wall;                 // ntv FP64 test vectors, contiguous
+    DevBuf P64all;               // ntv FP64 interpolation vectors
+    DevBuf PRall;                // ntv level-precision vectors (mixed only)
+    std::vector<DevBuf> V64;     // FGMRES Arnoldi basis (FP64)
+    std::vector<DevBuf> Z;       // FGMRES preconditioned vectors (level precision)
+    DevBuf x64, t64, q64;        // FP64 temporaries
+    DevBuf rR, zR, tR, eR;       // level-precision fine temporaries
+    std::vector<DevBuf> S;       // GMRES smoother basis
+    std::vector<DevBuf> CV;      // coarse GMRES basis
+    DevBuf rc, ec, ct;           // coarse vectors
+    DevBuf cgV, cgP;             // persistent coarse solver: basis, partial sums
+    std::vector<void *> W, P64, P;
+};
+
+static size_t f64_bytes(const Ctx &c) { return c.fine_ncpx() * sizeof(double2); }
+static size_t fR_bytes(const Ctx &c) { return c.fine_ncpx() * 2 * c.level_bytes(); }
+static size_t cR_bytes(const Ctx &c) { return c.coarse_ncpx() * 2 * c.level_bytes(); }
+
+void mg_alloc(Ctx &c) {
+    ensure_reduction(c, 64);
+    if (!c.work) c.work = new Ctx::Work();
+    Ctx::Work &w = *c.work;
+    const int ntv = c.prm.n_tv;
+    w.outer_m = c.prm.outer_restart;
+    w.coarse_m = c.prm.coarse_restart;
+    w.smooth_k = c.prm.gmres_smooth_k;
+    w.ntv = ntv;
+    w.mixed = c.mixed();
+    w.Wall.alloc(f64_bytes(c) * ntv);
+    w.P64all.alloc(f64_bytes(c) * ntv);
+    if (c.mixed()) w.PRall.alloc(fR_bytes(c) * ntv);
+    w.W.resize(ntv); w.P64.resize(ntv); w.P.resize(ntv);
+    for (int j = 0; j < ntv; ++j) {
+        w.W[j] = static_cast<char *>(w.Wall.p) + f64_bytes(c) * j;
+        w.P64[j] = static_cast<char *>(w.P64all.p) + f64_bytes(c) * j;
+        w.P[j] = c.mixed() ? static_cast<char *>(w.PRall.p) + fR_bytes(c) * j : w.P64[j];
+    }
+    w.V64.resize(w.outer_m + 1);
+    for (auto &b : w.V64) b.alloc(f64_bytes(c));
+    w.Z.resize(w.outer_m);
+    for (auto &b : w.Z) b.alloc(fR_bytes(c));
+    w.x64.alloc(f64_bytes(c)); w.t64.alloc(f64_bytes(c)); w.q64.alloc(f64_bytes(c));
+    w.rR.alloc(fR_bytes(c)); w.zR.alloc(fR_bytes(c)); w.tR.alloc(fR_bytes(c)); w.eR.alloc(fR_bytes(c));
+    if (c.prm.smoother == MGEIG_GMRES) {
+        w.S.resize(w.smooth_k + 1);
+        for (auto &b : w.S) b.alloc(fR_bytes(c));
+    }
+    w.CV.resize(w.coarse_m + 1);
+    for (auto &b : w.CV) b.alloc(cR_bytes(c));
+    w.rc.alloc(cR_bytes(c)); w.ec.alloc(cR_bytes(c)); w.ct.alloc(cR_bytes(c));
+    c.Dc.alloc((size_t)9 * c.nagg * 4 * ntv * ntv * 2 * c.level_bytes());
+}
+
+void mg_free(Ctx &c) {
+    if (!c.work) return;
+    Ctx::Work &w = *c.work;
+    w.Wall.free(); w.P64all.free(); w.PRall.free();
+    for (auto &b : w.V64) b.free();
+    for (auto &b : w.Z) b.free();
+    for (auto &b : w.S) b.free();
+    for (auto &b : w.CV) b.free();
+    w.x64.free(); w.t64.free(); w.q64.free();
+    w.rR.free(); w.zR.free(); w.tR.free(); w.eR.free();
+    w.rc.free(); w.ec.free(); w.ct.free();
+    w.cgV.free(); w.cgP.free();
+    delete c.work;
+    c.work = nullptr;
+    c.Dc.free();
+}
+
+void *mg_test_vector(Ctx &c, int j) { return c.work->W[j]; }
+
+// ---------------------------------------------------------------------------
+// Givens-based least squares of GMRES (host)
+
+struct Hess {
+    int m;
+    std::vector<cpx<double>> H;   // (m+1) x m, column-major
+    std::vector<double> cs;
+    std::vector<cpx<double>> sn, g;
+    explicit Hess(int m_) : m(m_), H((size_t)(m_ + 1) * m_), cs(m_), sn(m_), g(m_ + 1) {}
+    cpx<double> &h(int i, int j) { return H[(size_t)j * (m + 1) + i]; }
+    void start(double beta) { std::fill(g.begin(), g.end(), cpx<double>()); g[0] = cpx<double>(beta); }
+    // column j holds the new Hessenberg column (rows 0..j+1); returns |g_{j+1}|
+    double add_column(int j) {
+        for (int i = 0; i < j; ++i) {
+            cpx<double> a = h(i, j), b = h(i + 1, j);
+            h(i, j) = cs[i] * a + sn[i] * b;
+            h(i + 1, j) = cs[i] * b - conj(sn[i]) * a;
+        }
+        cpx<double> a = h(j, j), b = h(j + 1, j);
+        double aa = std::hypot(a.re, a.im), bb = std::hypot(b.re, b.im);
+        if (bb == 0) { cs[j] = 1; sn[j] = cpx<double>(); }
+        else if (aa == 0) { cs[j] = 0; sn[j] = cpx<double>(1); }
+        else {
+            double t = std::hypot(aa, bb);
+            cs[j] = aa / t;
+            sn[j] = (1.0 / t) * (cpx<double>(a.re / aa, a.im / aa) * conj(b));
+        }
+        h(j, j) = cs[j] * a + sn[j] * b;
+        h(j + 1, j) = cpx<double>();
+        g[j + 1] = -(conj(sn[j]) * g[j]);
+        g[j] = cs[j] * g[j];
+        return std::hypot(g[j + 1].re, g[j + 1].im);
+    }
+    std::vector<cpx<double>> solve(int k) {
+        std::vector<cpx<double>> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+            cpx<double> s = g[i];
+            for (int l = i + 1; l < k; ++l) s = s - h(i, l) * y[l];
+            cpx<double> d = h(i, i);
+            double dd = d.re * d.re + d.im * d.im;
+            y[i] = dd > 0 ? (1.0 / dd) * (s * conj(d)) : cpx<double>();
+        }
+        return y;
+    }
+};
+
+// Arnoldi step: w is orthogonalised against basis[0..j] (classical GS twice),
+// Hessenberg column j filled (rows 0..j+1).  Returns the norm of w.
+template <typename R>
+static double arnoldi_step(Ctx &c, std::vector<void *> &basis, int j, void *w, size_t n, Hess &H) {
+    std::vector<const void *> X(basis.begin(), basis.begin() + j + 1);
+    blas_multidot<R>(c, X.data(), j + 1, w, n, dslot(c, H1));
+    blas_multi_axpy<R>(c, w, X.data(), j + 1, dslot(c, H1), -1.0, n);
+    blas_multidot<R>(c, X.data(), j + 1, w, n, dslot(c, H2));
+    blas_multi_axpy<R>(c, w, X.data(), j + 1, dslot(c, H2), -1.0, n);
+    blas_norm2<R>(c, w, n, dslot(c, HN));
+    fetch(c, HN + 1);
+    for (int i = 0; i <= j; ++i) {
+        cpx<double> v = *hslot(c, H1 + i) + *hslot(c, H2 + i);
+        MG_REQUIRE(finite(v), MGEIG_EBREAKDOWN);
+        H.h(i, j) = v;
+    }
+    double nrm = std::sqrt(std::max(0.0, hslot(c, HN)->re));
+    MG_REQUIRE(std::isfinite(nrm), MGEIG_EBREAKDOWN);
+    H.h(j + 1, j) = cpx<double>(nrm);
+    return nrm;
+}
+
+// Restarted GMRES on flat arrays of precision R.  x is the initial guess when
+// x_nonzero, else it is set to the solution from zero.  tol = 0 runs exactly
+// maxiter steps.  Returns the iteration count.
+template <typename R, typename Op>
+static int gmres(Ctx &c, Op op, const void *b, void *x, bool x_nonzero, size_t n, double tol, int restart,
+                 int maxiter, std::vector<DevBuf> &basis_buf) {
+    std::vector<void *> basis;
+    for (auto &d : basis_buf) basis.push_back(d.p);
+    const int m = std::min<int>(restart, (int)basis.size() - 1);
+    blas_norm2<R>(c, b, n, dslot(c, HN));
+    fetch(c, HN + 1);
+    const double bnorm = std::sqrt(hslot(c, HN)->re);
+    MG_REQUIRE(std::isfinite(bnorm), MGEIG_EBREAKDOWN);
+    if (!x_nonzero) blas_zero<R>(c, x, n);
+    if (bnorm == 0) return 0;
+    int its = 0;
+    bool have_x = x_nonzero;
+    Hess H(m);
+    while (its < maxiter) {
+        if (have_x) {
+            op(x, basis[0]);
+            // basis0 = b - A x
+            blas_scale<R>(c, cpx<double>(-1), basis[0], n);
+            blas_axpy<R>(c, cpx<double>(1), b, basis[0], n);
+        } else {
+            blas_copy<R>(c, b, basis[0], n);
+        }
+        blas_norm2<R>(c, basis[0], n, dslot(c, HN));
+        fetch(c, HN + 1);
+        const double beta = std::sqrt(hslot(c, HN)->re);
+        MG_REQUIRE(std::isfinite(beta), MGEIG_EBREAKDOWN);
+        if (beta <= tol * bnorm || beta == 0) break;
+        blas_scale<R>(c, cpx<double>(1.0 / beta), basis[0], n);
+        H.start(beta);
+        const int mm = std::min(m, maxiter - its);
+        int k = 0;
+        double est = beta;
+        for (int j = 0; j < mm; ++j) {
+            op(basis[j], basis[j + 1]);
+            const double nrm = arnoldi_step<R>(c, basis, j, basis[j + 1], n, H);
+            est = H.add_column(j);
+            k = j + 1;
+            if (est <= tol * bnorm || nrm == 0) break;
+            blas_scale<R>(c, cpx<double>(1.0 / nrm), basis[j + 1], n);
+        }
+        std::vector<cpx<double>> y = H.solve(k);
+        std::vector<const void *> X(basis.begin(), basis.begin() + k);
+        blas_multi_axpy<R>(c, x, X.data(), k, upload(c, y), 1.0, n);
+        have_x = true;
+        its += k;
+        if (est <= tol * bnorm) break;
+    }
+    return its;
+}
+
+// ---------------------------------------------------------------------------
+// the two-grid cycle
+
+// coarse solve: one persistent cooperative launch when the restart length
+// fits it (the default), else the host-driven GMRES on the coarse kernels
+template <typename R>
+static void coarse_solve(Ctx &c, double sigma, const void *rc, void *ec) {
+    Ctx::Work &w = *c.work;
+    if (c.prm.coarse_restart <= COARSE_PERSISTENT_MAXM) {
+        coarse_gmres_persistent<R>(c, sigma, rc, ec, w.cgV, w.cgP, dslot(c, CGS));
+        return;
+    }
+    auto op = [&](const void *x, void *y) { coarse_apply<R>(c, c.Dc.p, sigma, x, y); };
+    int its = gmres<R>(c, op, rc, ec, false, c.coarse_ncpx(), c.prm.coarse_tol, c.prm.coarse_restart,
+                       c.prm.coarse_maxiter, w.CV);
+    c.st.coarse_iters += its;
+}
+
+// Adds the persistent coarse solver's iterations since the last call to the
+// stats (and their coarse-operator bytes to the timer); raises its errors.
+void coarse_iters_take(Ctx &c) {
+    if (!c.red_out.p) return;
+    CoarseState s;
+    MG_CUDA(cudaMemcpyAsync(&s, dslot(c, CGS), sizeof(s), cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+    MG_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(dslot(c, CGS)) + offsetof(CoarseState, iters), 0, sizeof(int),
+                            c.stream));
+    if (s.status != 0) MG_CUDA(cudaMemsetAsync(dslot(c, CGS), 0, sizeof(CoarseState), c.stream));
+    sync(c);
+    c.st.coarse_iters += s.iters;
+    const double ntv = c.prm.n_tv;
+    c.timer.total_bytes[K_COARSE_SOLVE] += (double)s.iters * 9.0 * c.nagg * 4 * ntv * ntv * 2 * c.level_bytes();
+    if (s.status == 1) throw Error{MGEIG_ETIMEOUT};
+    if (s.status != 0) throw Error{MGEIG_EBREAKDOWN};
+}
+
+// z = B r for fine vectors r, z of precision R (r is not modified)
+template <typename R>
+static void mg_cycle(Ctx &c, double sigma, const void *r, void *z) {
+    Ctx::Work &w = *c.work;
+    c.st.mg_cycles += 1;
+    restrict_vec<R>(c, (const void *const *)w.P.data(), r, w.rc.p);
+    coarse_solve<R>(c, sigma, w.rc.p, w.ec.p);
+    prolong_vec<R>(c, (const void *const *)w.P.data(), w.ec.p, z);
+    if (c.prm.smoother == MGEIG_SAP) {
+        for (int k = 0; k < c.prm.sap_cycles; ++k) {
+            sap_sweep<R>(c, 0, sigma, r, true, z);
+            sap_sweep<R>(c, 1, sigma, r, true, z);
+        }
+    } else {
+        const size_t n = c.fine_ncpx();
+        auto op = [&](const void *x, void *y) { apply_fine<R>(c, MODE_QSIGMA, sigma, x, y); };
+        for (int k = 0; k < c.prm.smooth_steps; ++k) {
+            // tR = r - A z ; eR = GMRES_k(A, tR) ; z += eR
+            apply_fine<R>(c, MODE_QSIGMA, sigma, z, w.tR.p);
+            blas_scale<R>(c, cpx<double>(-1), w.tR.p, n);
+            blas_axpy<R>(c, cpx<double>(1), r, w.tR.p, n);
+            gmres<R>(c, op, w.tR.p, w.eR.p, false, n, 0.0, c.prm.gmres_smooth_k, c.prm.gmres_smooth_k, w.S);
+            blas_axpy<R>(c, cpx<double>(1), w.eR.p, z, n);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P and the coarse operator from the test vectors
+
+void mg_rebuild(Ctx &c) {
+    Ctx::Work &w = *c.work;
+    const int ntv = c.prm.n_tv;
+    build_interp<double>(c, (const void *const *)w.W.data(), ntv, w.P64.data());
+    if (c.mixed()) {
+        for (int j = 0; j < ntv; ++j) convert_f64_to_f32(c, w.P64[j], w.P[j], c.fine_ncpx());
+        build_coarse<float>(c, (const void *const *)w.P.data(), c.Dc.p);
+    } else {
+        build_coarse<double>(c, (const void *const *)w.P.data(), c.Dc.p);
+    }
+}
+
+// Gram-Schmidt (each step twice) of FP64 vectors v[0..n) in place
+static void orthonormalise(Ctx &c, std::vector<void *> &v, int n) {
+    const size_t N = c.fine_ncpx();
+    for (int j = 0; j < n; ++j) {
+        if (j > 0) {
+            std::vector<const void *> X(v.begin(), v.begin() + j);
+            for (int pass = 0; pass < 2; ++pass) {
+                blas_multidot<double>(c, X.data(), j, v[j], N, dslot(c, H1));
+                blas_multi_axpy<double>(c, v[j], X.data(), j, dslot(c, H1), -1.0, N);
+            }
+        }
+        blas_norm2<double>(c, v[j], N, dslot(c, HN));
+        fetch(c, HN + 1);
+        const double nrm = std::sqrt(hslot(c, HN)->re);
+        MG_REQUIRE(std::isfinite(nrm) && nrm > 0, MGEIG_EBREAKDOWN);
+        blas_scale<double>(c, cpx<double>(1.0 / nrm), v[j], N);
+    }
+}
+
+// one preconditioner application on an FP64 fine vector, FP64 result
+template <typename R>
+static void mg_cycle_f64(Ctx &c, double sigma, const void *r64, void *z64) {
+    Ctx::Work &w = *c.work;
+    if (sizeof(R) == 4) {
+        convert_f64_to_f32(c, r64, w.rR.p, c.fine_ncpx());
+        mg_cycle<R>(c, sigma, w.rR.p, w.zR.p);
+        convert_f32_to_f64(c, w.zR.p, z64, c.fine_ncpx());
+    } else {
+        mg_cycle<R>(c, sigma, r64, z64);
+    }
+}
+
+template <typename R>
+static void smooth_random(Ctx &c, void *w64) {
+    Ctx::Work &w = *c.work;
+    const size_t n = c.fine_ncpx();
+    void *rhs = w.rR.p, *z = w.zR.p;
+    if (sizeof(R) == 4) convert_f64_to_f32(c, w64, rhs, n);
+    else blas_copy<double>(c, w64, rhs, n);
+    if (c.prm.smoother == MGEIG_SAP) {
+        blas_zero<R>(c, z, n);
+        for (int k = 0; k < c.prm.setup_smooth; ++k) {
+            sap_sweep<R>(c, 0, 0.0, rhs, true, z);
+            sap_sweep<R>(c, 1, 0.0, rhs, true, z);
+        }
+    } else {
+        auto op = [&](const void *x, void *y) { apply_fine<R>(c, MODE_QSIGMA, 0.0, x, y); };
+        gmres<R>(c, op, rhs, z, false, n, 0.0, c.prm.gmres_smooth_k, c.prm.gmres_smooth_k * c.prm.setup_smooth, w.S);
+    }
+    if (sizeof(R) == 4) convert_f32_to_f64(c, z, w64, n);
+    else blas_copy<double>(c, z, w64, n);
+}
+
+template <typename R>
+static void setup_impl(Ctx &c, uint64_t seed) {
+    Ctx::Work &w = *c.work;
+    const int ntv = c.prm.n_tv;
+    random_spinors(c, seed, w.Wall.p, ntv);
+    for (int j = 0; j < ntv; ++j) smooth_random<R>(c, w.W[j]);
+    orthonormalise(c, w.W, ntv);
+    mg_rebuild(c);
+    for (int it = 0; it < c.prm.setup_iters; ++it) {
+        for (int j = 0; j < ntv; ++j) {
+            mg_cycle_f64<R>(c, 0.0, w.W[j], w.t64.p);
+            blas_copy<double>(c, w.t64.p, w.W[j], c.fine_ncpx());
+        }
+        orthonormalise(c, w.W, ntv);
+        mg_rebuild(c);
+    }
+    sync(c);
+}
+
+void setup(Ctx &c, uint64_t seed) {
+    if (c.mixed()) setup_impl<float>(c, seed);
+    else setup_impl<double>(c, seed);
+    c.have_setup = true;
+}
+
+// ---------------------------------------------------------------------------
+// FGMRES (FP64) with the two-grid preconditioner
+
+template <typename R>
+static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol) {
+    Ctx::Work &w = *c.work;
+    const size_t n = c.fine_ncpx();
+    const int m = w.outer_m;
+    std::vector<void *> V;
+    for (auto &d : w.V64) V.push_back(d.p);
+    blas_norm2<double>(c, b, n, dslot(c, HN));
+    fetch(c, HN + 1);
+    const double bnorm = std::sqrt(hslot(c, HN)->re);
+    MG_REQUIRE(std::isfinite(bnorm), MGEIG_EBREAKDOWN);
+    blas_zero<double>(c, x, n);
+    if (bnorm == 0) return MGEIG_OK;
+    int its = 0;
+    bool have_x = false;
+    Hess H(m);
+    while (its < c.prm.outer_maxiter) {
+        if (have_x) {
+            apply_fine<double>(c, MODE_QSIGMA, sigma, x, V[0]);
+            blas_scale<double>(c, cpx<double>(-1), V[0], n);
+            blas_axpy<double>(c, cpx<double>(1), b, V[0], n);
+        } else {
+            blas_copy<double>(c, b, V[0], n);
+        }
+        blas_norm2<double>(c, V[0], n, dslot(c, HN));
+        fetch(c, HN + 1);
+        const double beta = std::sqrt(hslot(c, HN)->re);
+        MG_REQUIRE(std::isfinite(beta), MGEIG_EBREAKDOWN);
+        if (beta <= tol * bnorm) return MGEIG_OK;
+        blas_scale<double>(c, cpx<double>(1.0 / beta), V[0], n);
+        H.start(beta);
+        const int mm = std::min(m, c.prm.outer_maxiter - its);
+        int k = 0;
+        double est = beta;
+        for (int j = 0; j < mm; ++j) {
+            void *zj = w.Z[j].p;
+            if (sizeof(R) == 4) {
+                convert_f64_to_f32(c, V[j], w.rR.p, n);
+                mg_cycle<R>(c, sigma, w.rR.p, zj);
+                apply_fine_f64_from_f32(c, MODE_QSIGMA, sigma, zj, V[j + 1]);
+            } else {
+                mg_cycle<R>(c, sigma, V[j], zj);
+                apply_fine<double>(c, MODE_QSIGMA, sigma, zj, V[j + 1]);
+            }
+            const double nrm = arnoldi_step<double>(c, V, j, V[j + 1], n, H);
+            est = H.add_column(j);
+            k = j + 1;
+            c.st.outer_iters += 1;
+            if (est <= tol * bnorm || nrm == 0) break;
+            blas_scale<double>(c, cpx<double>(1.0 / nrm), V[j + 1], n);
+        }
+        std::vector<cpx<double>> y = H.solve(k);
+        for (int i = 0; i < k; ++i) blas_axpy_to_f64<R>(c, y[i], w.Z[i].p, x, n);
+        have_x = true;
+        its += k;
+        if (est <= tol * bnorm) return MGEIG_OK;
+    }
+    return MGEIG_ENOCONV;
+}
+
+int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol) {
+    c.st.solves += 1;
+    return c.mixed() ? fgmres_impl<float>(c, sigma, b64, x64, tol) : fgmres_impl<double>(c, sigma, b64, x64, tol);
+}
+
+// ---------------------------------------------------------------------------
+// small dense Hermitian eigenproblem (cyclic Jacobi), for the Ritz rotation
+
+static void herm_eig(int n, std::vector<cpx<double>> A, std::vector<double> &w, std::vector<cpx<double>> &Vm) {
+    auto a = [&](int i, int j) -> cpx<double> & { return A[(size_t)i * n + j]; };
+    Vm.assign((size_t)n * n, cpx<double>());
+    for (int i = 0; i < n; ++i) Vm[(size_t)i * n + i] = cpx<double>(1);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double m2 = a(i, j).re * a(i, j).re + a(i, j).im * a(i, j).im;
+                tot += m2;
+                if (i != j) off += m2;
+            }
+        if (off <= 1e-32 * tot || off == 0) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                cpx<double> apq = a(p, q);
+                double mag = std::hypot(apq.re, apq.im);
+                if (mag == 0) continue;
+                cpx<double> e(apq.re / mag, apq.im / mag);   // e^{i phi}
+                double app = a(p, p).re, aqq = a(q, q).re;
+                double theta = (aqq - app) / (2 * mag);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
+                double cth = 1 / std::sqrt(t * t + 1), sth = t * cth;
+                // G = [[c, s], [-s e^{-i phi}, c e^{-i phi}]] on (p, q); A <- G^dag A G, V <- V G
+                cpx<double> em = conj(e);
+                for (int k = 0; k < n; ++k) {
+                    cpx<double> akp = a(k, p), akq = a(k, q);
+                    a(k, p) = cth * akp - sth * (em * akq);
+                    a(k, q) = sth * akp + cth * (em * akq);
+                    cpx<double> vkp = Vm[(size_t)k * n + p], vkq = Vm[(size_t)k * n + q];
+                    Vm[(size_t)k * n + p] = cth * vkp - sth * (em * vkq);
+                    Vm[(size_t)k * n + q] = sth * vkp + cth * (em * vkq);
+                }
+                for (int k = 0; k < n; ++k) {
+                    cpx<double> apk = a(p, k), aqk = a(q, k);
+                    a(p, k) = cth * apk - sth * (e * aqk);
+                    a(q, k) = sth * apk + cth * (e * aqk);
+                }
+            }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = a(i, i).re;
+}
+
+// Ritz vectors of Q in span(W), ordered by |theta| then theta
+static void ritz_rotate(Ctx &c) {
+    Ctx::Work &w = *c.work;
+    const int n = c.prm.n_tv;
+    const size_t N = c.fine_ncpx();
+    std::vector<cpx<double>> H((size_t)n * n);
+    std::vector<const void *> X(w.W.begin(), w.W.end());
+    for (int j = 0; j < n; ++j) {
+        apply_fine<double>(c, MODE_QSIGMA, 0.0, w.W[j], w.q64.p);
+        blas_multidot<double>(c, X.data(), n, w.q64.p, N, dslot(c, H1));
+        fetch(c, n);
+        for (int i = 0; i < n; ++i) H[(size_t)i * n + j] = *hslot(c, H1 + i);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            cpx<double> s = 0.5 * (H[(size_t)i * n + j] + conj(H[(size_t)j * n + i]));
+            H[(size_t)i * n + j] = s;
+            H[(size_t)j * n + i] = conj(s);
+        }
+    std::vector<double> th;
+    std::vector<cpx<double>> Y;
+    herm_eig(n, H, th, Y);
+    std::vector<int> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+        double fa = std::fabs(th[a]), fb = std::fabs(th[b]);
+        return fa != fb ? fa < fb : th[a] < th[b];
+    });
+    // new vectors into the P64 area (scratch here), then copy back
+    for (int k = 0; k < n; ++k) {
+        std::vector<cpx<double>> coef(n);
+        for (int i = 0; i < n; ++i) coef[i] = Y[(size_t)i * n + ord[k]];
+        blas_zero<double>(c, w.P64[k], N);
+        blas_multi_axpy<double>(c, w.P64[k], X.data(), n, upload(c, coef), 1.0, N);
+    }
+    for (int k = 0; k < n; ++k) blas_copy<double>(c, w.P64[k], w.W[k], N);
+}
+
+// lambda = <v|Q v>, eps^2 = ||Q v - lambda v||^2 ; returns (lambda, eps)
+static std::pair<double, double> rayleigh(Ctx &c, const void *v) {
+    Ctx::Work &w = *c.work;
+    const size_t N = c.fine_ncpx();
+    apply_fine<double>(c, MODE_QSIGMA, 0.0, v, w.q64.p);
+    const void *X[1] = {v};
+    blas_multidot<double>(c, X, 1, w.q64.p, N, dslot(c, H1));
+    blas_resid_norm2(c, w.q64.p, v, dslot(c, H1), N, dslot(c, HN));
+    fetch(c, HN + 1);
+    const double lam = hslot(c, H1)->re;
+    const double eps = std::sqrt(std::max(0.0, hslot(c, HN)->re));
+    MG_REQUIRE(std::isfinite(lam) && std::isfinite(eps), MGEIG_EBREAKDOWN);
+    return {lam, eps};
+}
+
+int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host, double *resid) {
+    Ctx::Work &w = *c.work;
+    const size_t N = c.fine_ncpx();
+    const int spare = c.prm.n_tv - n_want;
+    const int guard = c.prm.n_guard < 0 ? std::min(spare, n_want) : std::min(spare, c.prm.n_guard);
+    const int n_eig = n_want + guard;
+    ritz_rotate(c);
+    mg_rebuild(c);
+    std::vector<double> lam(n_eig, 0.0), eps(n_eig, 1.0);
+    int sweeps = 0;
+    auto unconverged = [&]() {
+        for (int i = 0; i < n_eig; ++i)
+            if (eps[i] > tol) return true;
+        return false;
+    };
+    int status = MGEIG_OK;
+    while (unconverged() && sweeps < c.prm.max_sweeps) {
+        ++sweeps;
+        for (int i = 0; i < n_eig; ++i) {
+            if (eps[i] <= tol) continue;
+            const double sigma = lam[i] * std::max(1.0 - eps[i], 0.0);
+            int rc = fgmres_solve(c, sigma, w.W[i], w.x64.p, c.prm.solve_tol);
+            if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
+            if (i > 0) {
+                std::vector<const void *> X(w.W.begin(), w.W.begin() + i);
+                for (int pass = 0; pass < 2; ++pass) {
+                    blas_multidot<double>(c, X.data(), i, w.x64.p, N, dslot(c, H1));
+                    blas_multi_axpy<double>(c, w.x64.p, X.data(), i, dslot(c, H1), -1.0, N);
+                }
+            }
+            blas_norm2<double>(c, w.x64.p, N, dslot(c, HN));
+            fetch(c, HN + 1);
+            const double nrm = std::sqrt(hslot(c, HN)->re);
+            MG_REQUIRE(std::isfinite(nrm) && nrm > 0, MGEIG_EBREAKDOWN);
+            blas_scale<double>(c, cpx<double>(1.0 / nrm), w.x64.p, N);
+            blas_copy<double>(c, w.x64.p, w.W[i], N);
+            mg_rebuild(c);
+            auto le = rayleigh(c, w.W[i]);
+            lam[i] = le.first;
+            eps[i] = le.second;
+        }
+    }
+    c.st.sweeps = sweeps;
+    if (unconverged()) status = MGEIG_ENOCONV;
+    // order by |lambda|, then lambda
+    std::vector<int> ord(n_eig);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+        double fa = std::fabs(lam[a]), fb = std::fabs(lam[b]);
+        return fa != fb ? fa < fb : lam[a] < lam[b];
+    });
+    for (int k = 0; k < n_want; ++k) {
+        if (evals) evals[k] = lam[ord[k]];
+        if (resid) resid[k] = eps[ord[k]];
+    }
+    if (evecs_host) {
+        // host layout, unit norm, largest-modulus component real positive
+        for (int k = 0; k < n_want; ++k) {
+            unpack_spinor_f64(c, w.W[ord[k]], static_cast<double *>(c.staging.p), 1);
+            MG_CUDA(cudaMemcpyAsync(evecs_host + (size_t)k * N * 2, c.staging.p, N * 16, cudaMemcpyDeviceToHost, c.stream));
+            sync(c);
+            double *v = evecs_host + (size_t)k * N * 2;
+            size_t best = 0;
+            double bm = -1;
+            for (size_t i = 0; i < N; ++i) {
+                double m2 = v[2 * i] * v[2 * i] + v[2 * i + 1] * v[2 * i + 1];
+                if (m2 > bm * (1 + 1e-12)) { bm = m2; best = i; }
+            }
+            const double mag = std::sqrt(bm);
+            const double pr = v[2 * best] / mag, pi = -v[2 * best + 1] / mag;   // conj phase
+            for (size_t i = 0; i < N; ++i) {
+                double re = v[2 * i], im = v[2 * i + 1];
+                v[2 * i] = re * pr - im * pi;
+                v[2 * i + 1] = re * pi + im * pr;
+            }
+        }
+    }
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// single-step entry points used for parity checks (FP64 in / out)
+
+template <typename R>
+static void to_level(Ctx &c, const void *in64, void *outR) {
+    if (sizeof(R) == 4) convert_f64_to_f32(c, in64, outR, c.fine_ncpx());
+    else blas_copy<double>(c, in64, outR, c.fine_ncpx());
+}
+template <typename R>
+static void from_level(Ctx &c, const void *inR, void *out64) {
+    if (sizeof(R) == 4) convert_f32_to_f64(c, inR, out64, c.fine_ncpx());
+    else blas_copy<double>(c, inR, out64, c.fine_ncpx());
+}
+
+void sap_smooth_f64(Ctx &c, double sigma, const void *b64, void *z64, int cycles) {
+    Ctx::Work &w = *c.work;
+    if (c.mixed()) {
+        to_level<float>(c, b64, w.rR.p);
+        to_level<float>(c, z64, w.zR.p);
+        for (int k = 0; k < cycles; ++k) {
+            sap_sweep<float>(c, 0, sigma, w.rR.p, false, w.zR.p);
+            sap_sweep<float>(c, 1, sigma, w.rR.p, false, w.zR.p);
+        }
+        from_level<float>(c, w.zR.p, z64);
+    } else {
+        for (int k = 0; k < cycles; ++k) {
+            sap_sweep<double>(c, 0, sigma, b64, false, z64);
+            sap_sweep<double>(c, 1, sigma, b64, false, z64);
+        }
+    }
+}
+
+void mg_cycle_host(Ctx &c, double sigma, const double *r64, double *z64) {
+    if (c.mixed()) mg_cycle_f64<float>(c, sigma, r64, z64);
+    else mg_cycle_f64<double>(c, sigma, r64, z64);
+}
+
+// coarse vectors: FP64 flat <-> level precision flat
+__global__ void flat_f64_to_f32(size_t n, const double2 *in, float2 *out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+__global__ void flat_f32_to_f64(size_t n, const float2 *in, double2 *out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_double2(in[i].x, in[i].y);
+}
+
+static void coarse_in(Ctx &c, const void *x64, void *xR) {
+    const size_t n = c.coarse_ncpx();
+    if (c.mixed()) flat_f64_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, (const double2 *)x64, (float2 *)xR);
+    else MG_CUDA(cudaMemcpyAsync(xR, x64, n * 16, cudaMemcpyDeviceToDevice, c.stream));
+    MG_CHECK_LAUNCH();
+}
+static void coarse_out(Ctx &c, const void *xR, void *x64) {
+    const size_t n = c.coarse_ncpx();
+    if (c.mixed()) flat_f32_to_f64<<<grid_for(n, 256), 256, 0, c.stream>>>(n, (const float2 *)xR, (double2 *)x64);
+    else MG_CUDA(cudaMemcpyAsync(x64, xR, n * 16, cudaMemcpyDeviceToDevice, c.stream));
+    MG_CHECK_LAUNCH();
+}
+
+void coarse_apply_f64(Ctx &c, double sigma, const void *x64, void *y64) {
+    Ctx::Work &w = *c.work;
+    coarse_in(c, x64, w.rc.p);
+    if (c.mixed()) coarse_apply<float>(c, c.Dc.p, sigma, w.rc.p, w.ec.p);
+    else coarse_apply<double>(c, c.Dc.p, sigma, w.rc.p, w.ec.p);
+    coarse_out(c, w.ec.p, y64);
+}
+
+void restrict_f64(Ctx &c, const void *r64, void *rc64) {
+    Ctx::Work &w = *c.work;
+    if (c.mixed()) {
+        to_level<float>(c, r64, w.rR.p);
+        restrict_vec<float>(c, (const void *const *)w.P.data(), w.rR.p, w.rc.p);
+    } else {
+        restrict_vec<double>(c, (const void *const *)w.P.data(), r64, w.rc.p);
+    }
+    coarse_out(c, w.rc.p, rc64);
+}
+
+void prolong_f64(Ctx &c, const void *ec64, void *e64) {
+    Ctx::Work &w = *c.work;
+    coarse_in(c, ec64, w.ec.p);
+    if (c.mixed()) {
+        prolong_vec<float>(c, (const void *const *)w.P.data(), w.ec.p, w.zR.p);
+        from_level<float>(c, w.zR.p, e64);
+    } else {
+        prolong_vec<double>(c, (const void *const *)w.P.data(), w.ec.p, e64);
+    }
+}
+
+__global__ void dc_to_f64(size_t n, const float2 *in, double2 *out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_double2(in[i].x, in[i].y);
+}
+// column-major blocks -> row-major [9][nagg][row][col]
+__global__ void dc_transpose(size_t nblk, int n2, const double2 *in, double2 *out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t per = (size_t)n2 * n2;
+    if (i >= nblk * per) return;
+    size_t b = i / per, o = i % per;
+    int row = (int)(o / n2), col = (int)(o % n2);
+    out[i] = in[b * per + (size_t)col * n2 + row];
+}
+
+void coarse_op_f64(Ctx &c, void *out64) {
+    const int n2 = 2 * c.prm.n_tv;
+    const size_t nblk = (size_t)9 * c.nagg, tot = nblk * n2 * n2;
+    TmpBuf tmp;
+    tmp.alloc(tot * 16);
+    if (c.mixed()) dc_to_f64<<<grid_for(tot, 256), 256, 0, c.stream>>>(tot, c.Dc.as<float2>(), tmp.as<double2>());
+    else MG_CUDA(cudaMemcpyAsync(tmp.p, c.Dc.p, tot * 16, cudaMemcpyDeviceToDevice, c.stream));
+    dc_transpose<<<grid_for(tot, 256), 256, 0, c.stream>>>(nblk, n2, tmp.as<double2>(), static_cast<double2 *>(out64));
+    MG_CHECK_LAUNCH();
+    sync(c);
+    tmp.free();
+}
+
+void interp_f64(Ctx &c, void *const *out64) {
+    Ctx::Work &w = *c.work;
+    for (int j = 0; j < c.prm.n_tv; ++j)
+        MG_CUDA(cudaMemcpyAsync(out64[j], w.P64[j], f64_bytes(c), cudaMemcpyDeviceToDevice, c.stream));
+}
+
+}  // namespace mgeig
