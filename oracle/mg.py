@@ -191,6 +191,13 @@ class CoarseOperator:
         y = self.D(x).reshape(x.shape[0], 2 * self.ntv) * self.g5
         return y.reshape(x.shape) - sigma * x
 
+    def gamma5(self, x: np.ndarray) -> np.ndarray:
+        return (x.reshape(x.shape[0], 2 * self.ntv) * self.g5).reshape(x.shape)
+
+    def apply_dsigma(self, x: np.ndarray, sigma: float) -> np.ndarray:
+        """(D_c - sigma gamma5^c) x = gamma5^c (Q_c - sigma) x."""
+        return self.D(x) - sigma * self.gamma5(x)
+
 
 # ----------------------------------------------------------------------------
 # SAP smoother on D_sigma (Schwarz alternating procedure, Sec. 2)
@@ -257,7 +264,8 @@ class SAP:
 class TwoGrid:
     """The preconditioner B ~ (Q - sigma)^-1 of one FGMRES step.
 
-    B r = coarse correction x = P (Q_c - sigma)^-1 P^dag r (coarse GMRES), then nu
+    B r = coarse correction x = P (Q_c - sigma)^-1 P^dag r (coarse GMRES on the
+    equivalent D_c form, see coarse_solve), then nu
     post-smoothing steps on (Q - sigma) z = r from z = x: SAP cycles on
     D_sigma z = gamma5 r, or GMRES(k) restarts on Q - sigma.
     """
@@ -274,7 +282,11 @@ class TwoGrid:
         self.coarse = CoarseOperator(self.Dc, self.P.cdims, self.P.ntv)
 
     def coarse_solve(self, rc: np.ndarray, sigma: float) -> np.ndarray:
-        ec, _ = krylov.gmres(lambda v: self.coarse.apply(v, sigma), rc,
+        """(Q_c - sigma) e = r_c, solved by GMRES in the equivalent form
+        (D_c - sigma gamma5^c) e = gamma5^c r_c (Q_c - sigma = gamma5^c (D_c - sigma gamma5^c),
+        Eq. 2.6 with a shift): same solution, a spectrum in the right half plane
+        instead of the indefinite one of Q_c - sigma."""
+        ec, _ = krylov.gmres(lambda v: self.coarse.apply_dsigma(v, sigma), self.coarse.gamma5(rc),
                              tol=self.p["coarse_tol"], restart=self.p["coarse_restart"],
                              maxiter=self.p["coarse_maxiter"])
         return ec

@@ -10,7 +10,10 @@ sigma = 0.
 
 Before the iteration the test vectors are rotated to the Ritz vectors of Q in
 their span and ordered by |theta| (same span, hence the same P); the first
-N_eig are the start vectors v_i of Algorithm 1.
+N_eig + N_guard are the start vectors v_i of Algorithm 1, and the N_eig pairs of
+smallest |lambda| are returned.  The guard vectors (N_guard = min(N_tv - N_eig,
+N_eig) by default) lower the chance of missing a wanted pair, the failure the
+paper describes after Algorithm 1.
 
 Algorithm 1, per sweep over the unconverged i:
     sigma   = lambda_i * max(1 - eps_i, 0)                 (damped shift)
@@ -119,9 +122,13 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
 
 
 def eigensolve(op: dirac.WilsonClover, W0: np.ndarray, n_eig: int, eps: float, params: dict,
-               max_sweeps: int = 50, log=None):
-    """Setup, Ritz rotation of the test vectors, then Algorithm 1."""
+               max_sweeps: int = 50, log=None, n_guard: int = -1):
+    """Setup, Ritz rotation of the test vectors, then Algorithm 1 on n_eig + n_guard vectors."""
     W, B = setup(op, W0, params)
     W, _ = ritz_rotate(op, W)
-    extra = W[n_eig:] if W.shape[0] > n_eig else None
-    return rqi(op, W[:n_eig], extra, B, n_eig, eps, params, max_sweeps, log)
+    spare = W.shape[0] - n_eig
+    guard = min(spare, n_eig) if n_guard < 0 else min(spare, n_guard)
+    n_run = n_eig + guard
+    extra = W[n_run:] if W.shape[0] > n_run else None
+    lam, V, res, st = rqi(op, W[:n_run], extra, B, n_run, eps, params, max_sweeps, log)
+    return lam[:n_eig], V[:n_eig], res[:n_eig], st

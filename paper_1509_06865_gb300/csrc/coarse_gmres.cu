@@ -1,6 +1,8 @@
-// Coarse-grid GMRES (the coarse solver of Sec. 2: restarted GMRES on
-// Q_c - sigma = gamma5^c D_c - sigma, Eq. 2.6) as ONE persistent cooperative
-// launch: every Arnoldi step runs on the device, with no host round trip.
+// Coarse-grid GMRES (the coarse solver of Sec. 2) as ONE persistent
+// cooperative launch: every Arnoldi step runs on the device, with no host round
+// trip.  It solves (Q_c - sigma) e = r_c in the equivalent form
+// (D_c - sigma gamma5^c) e = gamma5^c r_c (Q_c - sigma = gamma5^c (D_c - sigma
+// gamma5^c), Eq. 2.6 with a shift).
 //
 // Grid: G co-resident blocks (cooperative launch); block b owns a contiguous
 // slice of coarse rows.  One Arnoldi step = the coarse matvec on the owned rows
@@ -86,7 +88,7 @@ __device__ __forceinline__ cpx<double> ldcg(const cpx<double> *p) {
     return cpx<double>(v.x, v.y);
 }
 
-// y[row] = (gamma5^c D_c - sigma) v (v scaled by s) for one row
+// y[row] = (D_c - sigma gamma5^c) v (v scaled by s) for one row
 template <typename R>
 __device__ __forceinline__ cpx<R> coarse_row(const CGArgs<R> &a, const cpx<R> *v, R s, int t) {
     const int n2 = 2 * a.ntv;
@@ -107,8 +109,8 @@ __device__ __forceinline__ cpx<R> coarse_row(const CGArgs<R> &a, const cpx<R> *v
 #pragma unroll 4
         for (int j = 0; j < n2; ++j) cmac(acc, blk[(size_t)j * n2], ldcg(xb + j));
     }
-    if (row >= a.ntv) acc = -acc;
-    return s * acc - (a.sigma * s) * ldcg(v + t);
+    const R sg = row >= a.ntv ? -a.sigma : a.sigma;
+    return s * acc - (sg * s) * ldcg(v + t);
 }
 
 // block-reduce `cnt` complex partials (one per thread-local value array) into
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
     {
         double acc = 0;
         for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-            cpx<R> v = a.b[t];
+            cpx<R> v = a.b[t];   // |gamma5^c b| = |b|
             acc += (double)v.re * v.re + (double)v.im * v.im;
             a.x[t] = cpx<R>();
         }
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
             double acc = 0;
             for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
                 cpx<R> r = a.b[t];
+                if ((t % (2 * a.ntv)) >= a.ntv) r = -r;    // gamma5^c r_c
                 if (have_x) r = r - coarse_row<R>(a, a.x, R(1), t);
                 a.V[t] = r;
                 acc += (double)r.re * r.re + (double)r.im * r.im;

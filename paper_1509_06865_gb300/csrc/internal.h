@@ -122,7 +122,8 @@ template <typename R> void build_interp(Ctx &c, const void *const *W64, int ntv,
 template <typename R> void restrict_vec(Ctx &c, const void *const *P, const void *r, void *rc);
 template <typename R> void prolong_vec(Ctx &c, const void *const *P, const void *ec, void *e);
 template <typename R> void build_coarse(Ctx &c, const void *const *P, void *Dc);
-template <typename R> void coarse_apply(Ctx &c, const void *Dc, double sigma, const void *x, void *y);
+template <typename R> void coarse_apply(Ctx &c, const void *Dc, double sigma, const void *x, void *y, bool dform = false);
+template <typename R> void coarse_gamma5(Ctx &c, const void *x, void *y);
 template <typename R> void sap_sweep(Ctx &c, int colour, double sigma, const void *rhs, bool rhs_gamma5, void *z);
 
 // ----- persistent coarse GMRES (coarse_gmres.cu) -----

@@ -383,9 +383,11 @@ void build_coarse(Ctx &c, const void *const *P, void *Dc) {
 // ---------------------------------------------------------------------------
 // coarse apply: thread per (coarse site, row)
 
+// dform = 0: y = (gamma5^c D_c - sigma) x = (Q_c - sigma) x
+// dform = 1: y = (D_c - sigma gamma5^c) x = gamma5^c (Q_c - sigma) x
 template <typename R>
 __global__ void coarse_apply_kernel(AggGeom A, int ntv, const cpx<R> *__restrict__ Dc, R sigma,
-                                    const cpx<R> *__restrict__ x, cpx<R> *__restrict__ y) {
+                                    const cpx<R> *__restrict__ x, cpx<R> *__restrict__ y, int dform) {
     const int n2 = 2 * ntv;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)A.n * n2) return;
@@ -405,18 +407,40 @@ __global__ void coarse_apply_kernel(AggGeom A, int ntv, const cpx<R> *__restrict
         const cpx<R> *xb = x + (size_t)b * n2;
         for (int j = 0; j < n2; ++j) cmac(acc, blk[(size_t)j * n2], xb[j]);
     }
-    if (row >= ntv) acc = -acc;
-    y[t] = acc - sigma * x[t];
+    if (dform) {
+        y[t] = acc - (row >= ntv ? -sigma : sigma) * x[t];
+    } else {
+        if (row >= ntv) acc = -acc;
+        y[t] = acc - sigma * x[t];
+    }
+}
+
+// y = gamma5^c x on coarse vectors
+template <typename R>
+__global__ void coarse_gamma5_kernel(size_t n, int ntv, const cpx<R> *__restrict__ x, cpx<R> *__restrict__ y) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int row = (int)(t % (2 * ntv));
+    y[t] = row >= ntv ? -x[t] : x[t];
 }
 
 template <typename R>
-void coarse_apply(Ctx &c, const void *Dc, double sigma, const void *x, void *y) {
+void coarse_gamma5(Ctx &c, const void *x, void *y) {
+    const size_t n = c.coarse_ncpx();
+    coarse_gamma5_kernel<R><<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.prm.n_tv, static_cast<const cpx<R> *>(x),
+                                                                    static_cast<cpx<R> *>(y));
+    MG_CHECK_LAUNCH();
+}
+
+template <typename R>
+void coarse_apply(Ctx &c, const void *Dc, double sigma, const void *x, void *y, bool dform) {
     AggGeom A = make_agg(c, c.prm.agg);
     const int ntv = c.prm.n_tv;
     const size_t n = (size_t)A.n * 2 * ntv;
     TimeScope ts(c.timer, K_COARSE_APPLY, (double)A.n * (9.0 * 4 * ntv * ntv + 20.0 * ntv) * sizeof(cpx<R>));
     coarse_apply_kernel<R><<<grid_for(n, 128), 128, 0, c.stream>>>(A, ntv, static_cast<const cpx<R> *>(Dc), (R)sigma,
-                                                                   static_cast<const cpx<R> *>(x), static_cast<cpx<R> *>(y));
+                                                                   static_cast<const cpx<R> *>(x), static_cast<cpx<R> *>(y),
+                                                                   dform ? 1 : 0);
     MG_CHECK_LAUNCH();
 }
 
@@ -569,7 +593,8 @@ void sap_sweep(Ctx &c, int colour, double sigma, const void *rhs, bool rhs_gamma
     template void restrict_vec<R>(Ctx &, const void *const *, const void *, void *);         \
     template void prolong_vec<R>(Ctx &, const void *const *, const void *, void *);          \
     template void build_coarse<R>(Ctx &, const void *const *, void *);                       \
-    template void coarse_apply<R>(Ctx &, const void *, double, const void *, void *);        \
+    template void coarse_apply<R>(Ctx &, const void *, double, const void *, void *, bool);  \
+    template void coarse_gamma5<R>(Ctx &, const void *, void *);                             \
     template void sap_sweep<R>(Ctx &, int, double, const void *, bool, void *);
 INST(double)
 INST(float)

@@ -335,8 +335,11 @@ static int gmres(Ctx &c, Op op, const void *b, void *x, bool x_nonzero, size_t n
 // ---------------------------------------------------------------------------
 // the two-grid cycle
 
-// coarse solve: one persistent cooperative launch when the restart length
-// fits it (the default), else the host-driven GMRES on the coarse kernels
+// Coarse solve (Q_c - sigma) e = r_c.  GMRES runs on the equivalent system
+// (D_c - sigma gamma5^c) e = gamma5^c r_c (Q_c - sigma = gamma5^c (D_c - sigma
+// gamma5^c), Eq. 2.6 with a shift), whose spectrum lies in the right half plane
+// instead of around the origin.  One persistent cooperative launch when the
+// restart length fits it (the default), else the host-driven GMRES loop.
 template <typename R>
 static void coarse_solve(Ctx &c, double sigma, const void *rc, void *ec) {
     Ctx::Work &w = *c.work;
@@ -344,8 +347,9 @@ static void coarse_solve(Ctx &c, double sigma, const void *rc, void *ec) {
         coarse_gmres_persistent<R>(c, sigma, rc, ec, w.cgV, w.cgP, dslot(c, CGS));
         return;
     }
-    auto op = [&](const void *x, void *y) { coarse_apply<R>(c, c.Dc.p, sigma, x, y); };
-    int its = gmres<R>(c, op, rc, ec, false, c.coarse_ncpx(), c.prm.coarse_tol, c.prm.coarse_restart,
+    coarse_gamma5<R>(c, rc, w.ct.p);
+    auto op = [&](const void *x, void *y) { coarse_apply<R>(c, c.Dc.p, sigma, x, y, true); };
+    int its = gmres<R>(c, op, w.ct.p, ec, false, c.coarse_ncpx(), c.prm.coarse_tol, c.prm.coarse_restart,
                        c.prm.coarse_maxiter, w.CV);
     c.st.coarse_iters += its;
 }

@@ -38,6 +38,7 @@ def test_eigensolve_config1(ref, precision, smoother):
     ctx.setup(c["seed"])
     lam, V, res, st = ctx.eigensolve(c["n_eig"], 1e-10)
     ctx.close()
+    print("stats", precision, smoother, st)
     assert st["converged"], st
     assert np.all(res <= 1e-10)
     want = w[:c["n_eig"]]
