@@ -89,7 +89,7 @@ typedef struct mgeig_params {
     int setup_iters;      /* setup: multigrid iterations per test vector        */
     int outer_restart;    /* FGMRES restart length                              */
     int outer_maxiter;    /* FGMRES iteration cap per solve                     */
-    int coarse_restart;   /* coarse GMRES restart length                        */
+    int coarse_restart;   /* coarse GMRES restart length (1..32)                */
     int coarse_maxiter;   /* coarse GMRES iteration cap per solve               */
     double coarse_tol;    /* coarse GMRES relative residual                     */
     double solve_tol;     /* FGMRES relative residual of each shifted solve     */
@@ -98,6 +98,8 @@ typedef struct mgeig_params {
     int max_sweeps;       /* Rayleigh quotient iteration: sweep cap             */
     int n_guard;          /* extra iterated vectors beyond n_eig (capped at
                              n_tv - n_eig); -1 = min(n_tv - n_eig, n_eig)       */
+    int coarse_deflate;   /* 1: the coarse solve treats span{P^dag w_j} of the
+                             test vectors exactly (Galerkin deflation), 0: plain */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */

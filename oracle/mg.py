@@ -264,10 +264,22 @@ class SAP:
 class TwoGrid:
     """The preconditioner B ~ (Q - sigma)^-1 of one FGMRES step.
 
-    B r = coarse correction x = P (Q_c - sigma)^-1 P^dag r (coarse GMRES on the
-    equivalent D_c form, see coarse_solve), then nu
-    post-smoothing steps on (Q - sigma) z = r from z = x: SAP cycles on
-    D_sigma z = gamma5 r, or GMRES(k) restarts on Q - sigma.
+    B r = coarse correction x = P (Q_c - sigma)^-1 P^dag r, then nu post-smoothing
+    steps on (Q - sigma) z = r from z = x: SAP cycles on D_sigma z = gamma5 r, or
+    GMRES(k) restarts on Q - sigma.
+
+    Coarse solve (Q_c - sigma) e = r_c, A = Q_c - sigma.  The test vectors w_j are
+    in range(P), so the coarse vectors W = [P^dag w_1 .. P^dag w_N] represent them
+    exactly and W^dag A W = (Ritz matrix of Q on span{w_j}) - sigma.  When the w_j
+    approximate eigenvectors (the Rayleigh quotient iteration puts its current
+    v_i there) and sigma approaches one of their eigenvalues, A is nearly singular
+    exactly on span(W).  That part is solved exactly (deflation): with
+    E = W^dag A W and Pi = 1 - A W E^-1 W^dag,
+        e = W E^-1 W^dag r_c + (1 - W E^-1 W^dag A) y,   Pi A y = Pi r_c,
+    and GMRES solves the projected system in the equivalent form
+    gamma5^c Pi A y = gamma5^c Pi r_c (gamma5^c A = D_c - sigma gamma5^c has its
+    spectrum in the right half plane; Eq. 2.6 with a shift).  With deflate=False
+    GMRES runs on (D_c - sigma gamma5^c) e = gamma5^c r_c directly.
     """
 
     def __init__(self, op: dirac.WilsonClover, W: np.ndarray, params: dict):
@@ -277,19 +289,40 @@ class TwoGrid:
         self.sap = SAP(op, self.p["sap_block"]) if self.p["smoother"] == "sap" else None
 
     def set_test_vectors(self, W: np.ndarray):
-        self.P = Interpolation(W, self.p["agg"])
+        self.W = np.array(W)
+        self.P = Interpolation(self.W, self.p["agg"])
         self.Dc = coarse_operator(self.op, self.P)
         self.coarse = CoarseOperator(self.Dc, self.P.cdims, self.P.ntv)
+        self._defl = None
+
+    def deflation(self, sigma: float):
+        """(W, A W, E^-1) for the current test vectors and shift."""
+        if self._defl is None or self._defl[0] != sigma:
+            Wc = [self.P.restrict(w) for w in self.W]
+            AW = [self.coarse.apply(x, sigma) for x in Wc]
+            E = np.array([[np.vdot(Wc[i], AW[j]) for j in range(len(Wc))] for i in range(len(Wc))])
+            self._defl = (sigma, Wc, AW, np.linalg.inv(E))
+        return self._defl[1:]
 
     def coarse_solve(self, rc: np.ndarray, sigma: float) -> np.ndarray:
-        """(Q_c - sigma) e = r_c, solved by GMRES in the equivalent form
-        (D_c - sigma gamma5^c) e = gamma5^c r_c (Q_c - sigma = gamma5^c (D_c - sigma gamma5^c),
-        Eq. 2.6 with a shift): same solution, a spectrum in the right half plane
-        instead of the indefinite one of Q_c - sigma."""
-        ec, _ = krylov.gmres(lambda v: self.coarse.apply_dsigma(v, sigma), self.coarse.gamma5(rc),
-                             tol=self.p["coarse_tol"], restart=self.p["coarse_restart"],
-                             maxiter=self.p["coarse_maxiter"])
-        return ec
+        C = self.coarse
+        gm = dict(tol=self.p["coarse_tol"], restart=self.p["coarse_restart"], maxiter=self.p["coarse_maxiter"])
+        if not self.p.get("coarse_deflate", True):
+            ec, _ = krylov.gmres(lambda v: C.apply_dsigma(v, sigma), C.gamma5(rc), **gm)
+            return ec
+        Wc, AW, Einv = self.deflation(sigma)
+
+        def coeff(u):                      # E^-1 W^dag u
+            return Einv @ np.array([np.vdot(w, u) for w in Wc])
+
+        def project(u):                    # Pi u = u - A W E^-1 W^dag u
+            t = coeff(u)
+            return u - sum(ti * awi for ti, awi in zip(t, AW))
+
+        y, _ = krylov.gmres(lambda v: C.gamma5(project(C.apply(v, sigma))), C.gamma5(project(rc)), **gm)
+        t0 = coeff(rc)
+        t1 = coeff(C.apply(y, sigma))
+        return y + sum((a - b) * w for a, b, w in zip(t0, t1, Wc))
 
     def __call__(self, r: np.ndarray, sigma: float) -> np.ndarray:
         x = self.P.prolong(self.coarse_solve(self.P.restrict(r), sigma))
@@ -316,6 +349,7 @@ DEFAULT_PARAMS = dict(
     coarse_tol=5e-2,
     coarse_restart=30,
     coarse_maxiter=300,
+    coarse_deflate=True,
     outer_restart=20,
     outer_maxiter=200,
     solve_tol=1e-2,

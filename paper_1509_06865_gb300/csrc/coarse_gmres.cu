@@ -1,31 +1,40 @@
-// Coarse-grid GMRES (the coarse solver of Sec. 2) as ONE persistent
-// cooperative launch: every Arnoldi step runs on the device, with no host round
-// trip.  It solves (Q_c - sigma) e = r_c in the equivalent form
-// (D_c - sigma gamma5^c) e = gamma5^c r_c (Q_c - sigma = gamma5^c (D_c - sigma
-// gamma5^c), Eq. 2.6 with a shift).
+// Coarse-grid solve of the two-grid cycle (Sec. 2: restarted GMRES as the
+// coarse solver for Q_c) as ONE persistent cooperative launch: every Arnoldi
+// step runs on the device, with no host round trip.
 //
-// Grid: G co-resident blocks (cooperative launch); block b owns a contiguous
-// slice of coarse rows.  One Arnoldi step = the coarse matvec on the owned rows
-// (reading the neighbours' rows written before the last grid barrier), two
-// classical Gram-Schmidt passes and a norm, i.e. three grid-wide reductions.
-// Partial sums go to a [G][slots] buffer; after each barrier every block adds
-// the G partials in the same order, so all blocks hold bit-identical Hessenberg
-// columns and run the Givens rotations and the final triangular solve
-// redundantly (no extra barrier, deterministic).  Basis vectors are kept
-// unnormalised with a scale factor each, so no barrier is needed between a
-// norm and the next matvec.
+// It solves (Q_c - sigma) e = r_c, A = Q_c - sigma = gamma5^c D_c - sigma.
+//  * Deflation (k > 0): W = [P^dag w_1 .. P^dag w_k] are the coarse images of the
+//    test vectors (the current eigenvector approximations of Algorithm 1), the
+//    directions on which A becomes nearly singular when sigma approaches their
+//    eigenvalues.  With E^-1 = (W^dag A W)^-1 (host-computed) and
+//    Pi = 1 - A W E^-1 W^dag:  e = W E^-1 W^dag r_c + (1 - W E^-1 W^dag A) y,
+//    where Pi A y = Pi r_c.
+//  * GMRES runs on gamma5^c Pi A y = gamma5^c Pi r_c, i.e. on the D_c form
+//    (gamma5^c A = D_c - sigma gamma5^c, Eq. 2.6 with a shift), whose spectrum
+//    lies in the right half plane instead of around the origin.
+//
+// Grid: G co-resident blocks; block b owns a contiguous slice of coarse rows.
+// One Arnoldi step = the coarse matvec on the owned rows (reading neighbour rows
+// written before the last grid barrier), the deflation projection, two classical
+// Gram-Schmidt passes and a norm: four grid-wide reductions.  Partial sums go to
+// a [G][slots] buffer; after each barrier every block adds the G partials in the
+// same order, so all blocks hold bit-identical scalars and run the Givens
+// rotations and the triangular solve redundantly (deterministic, no extra
+// barrier).  Basis vectors stay unnormalised with one scale factor each.
 //
 // The grid barrier spins on a generation counter with a clock64() budget; on
 // expiry it raises a sticky error word (the kernel then returns without further
-// waits) that the host reads at its next synchronisation and reports as
-// MGEIG_ETIMEOUT.  The same state block accumulates the iteration count.
+// waits) that the host reads at its next synchronisation (MGEIG_ETIMEOUT).
 #include "internal.h"
 
 namespace mgeig {
 
 constexpr int CG_THREADS = 256;
-constexpr int CG_MAXM = 32;                  // restart length limit of this kernel
-constexpr int CG_SLOTS = 2 * (CG_MAXM + 2) + 2;
+constexpr int CG_MAXM = COARSE_PERSISTENT_MAXM;   // restart length limit
+constexpr int CG_MAXK = 24;                       // deflation vectors (= max N_tv)
+constexpr int OFF_H1 = 0, OFF_H2 = CG_MAXM + 2, OFF_N = 2 * (CG_MAXM + 2), OFF_P = OFF_N + 2;
+constexpr int CG_SLOTS = OFF_P + CG_MAXK;
+constexpr int WS = CG_MAXM + 2;                   // per-warp scratch stride
 
 struct CGState {
     unsigned int count;   // barrier arrivals (returns to 0 after every barrier)
@@ -41,9 +50,13 @@ struct CGArgs {
     int cd[4];                     // coarse lattice extents
     const cpx<R> *Dc;              // [9][nagg][col][row]
     R sigma;
-    const cpx<R> *b;
-    cpx<R> *x;
+    const cpx<R> *b;               // r_c
+    cpx<R> *x;                     // e (output); holds y during the iteration
+    cpx<R> *rhs;                   // gamma5^c Pi r_c (scratch, n)
     cpx<R> *V;                     // (m + 1) x n
+    int k;                         // deflation vectors (0: none)
+    const cpx<R> *W, *AW;          // k x n each
+    const double2 *Einv;           // k x k, row-major
     double2 *partial;              // [G][CG_SLOTS]
     CGState *st;
     int m, maxiter;
@@ -67,7 +80,7 @@ __device__ __forceinline__ bool grid_sync(CGState *st, unsigned int nblocks, lon
             const long long t0 = clock64();
             while (*vgen == g0) {
                 if (clock64() - t0 > timeout) { atomicExch(&st->status, 1); break; }
-                __nanosleep(40);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -77,8 +90,8 @@ __device__ __forceinline__ bool grid_sync(CGState *st, unsigned int nblocks, lon
     return ok;
 }
 
-// Loads of data that other blocks wrote before the last grid barrier bypass
-// the (non-coherent) L1: ld.global.cg.
+// Loads of data other blocks wrote before the last grid barrier bypass the
+// (non-coherent) L1: ld.global.cg.
 __device__ __forceinline__ cpx<float> ldcg(const cpx<float> *p) {
     float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
     return cpx<float>(v.x, v.y);
@@ -88,14 +101,14 @@ __device__ __forceinline__ cpx<double> ldcg(const cpx<double> *p) {
     return cpx<double>(v.x, v.y);
 }
 
-// y[row] = (D_c - sigma gamma5^c) v (v scaled by s) for one row
+// row t of (Q_c - sigma)(s v) = (gamma5^c D_c - sigma)(s v)
 template <typename R>
-__device__ __forceinline__ cpx<R> coarse_row(const CGArgs<R> &a, const cpx<R> *v, R s, int t) {
+__device__ __forceinline__ cpx<R> qrow(const CGArgs<R> &a, const cpx<R> *v, R s, int t) {
     const int n2 = 2 * a.ntv;
     const int site = t / n2, row = t % n2;
     int ac[4], rem = site;
     for (int mu = 0; mu < 4; ++mu) { ac[mu] = rem % a.cd[mu]; rem /= a.cd[mu]; }
-    cpx<R> acc;
+    cpx<R> acc0, acc1;
     for (int d = 0; d < 9; ++d) {
         int nb = site;
         if (d > 0) {
@@ -106,43 +119,65 @@ __device__ __forceinline__ cpx<R> coarse_row(const CGArgs<R> &a, const cpx<R> *v
         }
         const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
         const cpx<R> *xb = v + (size_t)nb * n2;
-#pragma unroll 4
-        for (int j = 0; j < n2; ++j) cmac(acc, blk[(size_t)j * n2], ldcg(xb + j));
+        int j = 0;
+        for (; j + 1 < n2; j += 2) {
+            cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+            cmac(acc1, blk[(size_t)(j + 1) * n2], ldcg(xb + j + 1));
+        }
+        if (j < n2) cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
     }
-    const R sg = row >= a.ntv ? -a.sigma : a.sigma;
-    return s * acc - (sg * s) * ldcg(v + t);
+    cpx<R> acc = acc0 + acc1;
+    if (row >= a.ntv) acc = -acc;
+    return s * acc - (a.sigma * s) * ldcg(v + t);
 }
 
-// block-reduce `cnt` complex partials (one per thread-local value array) into
-// partial[blockIdx][off + i]
-__device__ __forceinline__ void block_partial(double re, double im, int i, double2 *sh, double2 *out) {
+template <typename R>
+__device__ __forceinline__ cpx<R> g5c(const CGArgs<R> &a, int t, cpx<R> v) {
+    return (t % (2 * a.ntv)) >= a.ntv ? -v : v;
+}
+
+// warp-reduce (re, im) and park it in sh[warp][i]
+__device__ __forceinline__ void warp_park(double re, double im, int i, double2 *sh) {
     for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) sh[w * (CG_MAXM + 2) + i] = make_double2(re, im);
-    (void)out;
+    if ((threadIdx.x & 31) == 0) sh[(threadIdx.x >> 5) * WS + i] = make_double2(re, im);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
-    __shared__ double2 wsum[(CG_THREADS / 32) * (CG_MAXM + 2)];
-    __shared__ double2 h[CG_MAXM + 2];
+    __shared__ double2 wsum[(CG_THREADS / 32) * WS];
+    __shared__ double2 h[WS];
     __shared__ double2 Rm[(CG_MAXM + 1) * CG_MAXM];   // rotated Hessenberg, column-major
     __shared__ double cs[CG_MAXM];
     __shared__ double2 sn[CG_MAXM], g[CG_MAXM + 1], y[CG_MAXM];
     __shared__ double scale[CG_MAXM + 1];
+    __shared__ double2 Ei[CG_MAXK * CG_MAXK], t0[CG_MAXK], tc[CG_MAXK];
     __shared__ double bnorm, beta;
-    __shared__ int stop, kcols;
+    __shared__ int stop;
     const unsigned int G = gridDim.x;
     const int nw = CG_THREADS / 32;
     const int rows_per_block = (a.n + G - 1) / G;
     const int r0 = blockIdx.x * rows_per_block;
     const int r1 = min(a.n, r0 + rows_per_block);
     double2 *mypart = a.partial + (size_t)blockIdx.x * CG_SLOTS;
+    const int k = a.k;
 
-    // sum partial[0..G)[off + i] for i < cnt into h[i] (all blocks, same order)
+    for (int i = threadIdx.x; i < k * k; i += blockDim.x) Ei[i] = a.Einv[i];
+    if (threadIdx.x < CG_MAXK) { tc[threadIdx.x] = make_double2(0, 0); t0[threadIdx.x] = make_double2(0, 0); }
+    __syncthreads();
+
+    // block partials in wsum[.][0..cnt) -> mypart[off..off+cnt)
+    auto flush = [&](int off, int cnt) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            double sr = 0, si = 0;
+            for (int w = 0; w < nw; ++w) { double2 p = wsum[w * WS + i]; sr += p.x; si += p.y; }
+            mypart[off + i] = make_double2(sr, si);
+        }
+    };
+    // after a barrier: h[i] = sum over blocks of partial[.][off + i]
     auto gather = [&](int off, int cnt) {
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             double sr = 0, si = 0;
@@ -154,69 +189,109 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
         }
         __syncthreads();
     };
-    // reduce per-thread values in wsum[w][i] (i < cnt) to mypart[off + i]
-    auto flush = [&](int off, int cnt) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    // tc = E^-1 W^dag u (grid-wide); u complete on the owned rows
+    auto deflation_coeffs = [&](const cpx<R> *u) -> bool {
+        for (int i = 0; i < k; ++i) {
+            const cpx<R> *wi = a.W + (size_t)i * a.n;
             double sr = 0, si = 0;
-            for (int w = 0; w < nw; ++w) { double2 p = wsum[w * (CG_MAXM + 2) + i]; sr += p.x; si += p.y; }
-            mypart[off + i] = make_double2(sr, si);
+            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
+                cpx<R> p = wi[t], q = u[t];
+                sr += (double)p.re * q.re + (double)p.im * q.im;
+                si += (double)p.re * q.im - (double)p.im * q.re;
+            }
+            warp_park(sr, si, i, wsum);
         }
+        flush(OFF_P, k);
+        if (!grid_sync(a.st, G, a.timeout)) return false;
+        gather(OFF_P, k);
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            double sr = 0, si = 0;
+            for (int l = 0; l < k; ++l) {
+                double2 e = Ei[i * k + l], d = h[l];
+                sr += e.x * d.x - e.y * d.y;
+                si += e.x * d.y + e.y * d.x;
+            }
+            tc[i] = make_double2(sr, si);
+        }
+        __syncthreads();
+        return true;
     };
-
-    // ||b||
-    {
+    // u <- gamma5^c (u - A W tc) on the owned rows
+    auto project_g5 = [&](cpx<R> *u) {
+        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
+            cpx<R> q = u[t];
+            for (int i = 0; i < k; ++i) {
+                const cpx<R> ti((R)tc[i].x, (R)tc[i].y);
+                q = q - ti * a.AW[(size_t)i * a.n + t];
+            }
+            u[t] = g5c(a, t, q);
+        }
+        __syncthreads();
+    };
+    // u = gamma5^c Pi (Q_c - sigma)(s v) on the owned rows
+    auto apply_op = [&](const cpx<R> *v, R s, cpx<R> *u) -> bool {
+        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) u[t] = qrow<R>(a, v, s, t);
+        __syncthreads();
+        if (k > 0 && !deflation_coeffs(u)) return false;
+        project_g5(u);
+        return true;
+    };
+    // h[0] = ||v||^2 over the grid
+    auto grid_norm2 = [&](const cpx<R> *v) -> bool {
         double acc = 0;
         for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-            cpx<R> v = a.b[t];   // |gamma5^c b| = |b|
-            acc += (double)v.re * v.re + (double)v.im * v.im;
-            a.x[t] = cpx<R>();
+            cpx<R> q = v[t];
+            acc += (double)q.re * q.re + (double)q.im * q.im;
         }
-        block_partial(acc, 0.0, 0, wsum, nullptr);
-        flush(2 * (CG_MAXM + 2), 1);
-        if (!grid_sync(a.st, G, a.timeout)) return;
-        gather(2 * (CG_MAXM + 2), 1);
-        if (threadIdx.x == 0) { bnorm = sqrt(h[0].x); stop = !(bnorm > 0); }
+        warp_park(acc, 0.0, 0, wsum);
+        flush(OFF_N, 1);
+        if (!grid_sync(a.st, G, a.timeout)) return false;
+        gather(OFF_N, 1);
+        return true;
+    };
+
+    // rhs = gamma5^c Pi r_c, t0 = E^-1 W^dag r_c, x = 0
+    for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) { a.rhs[t] = a.b[t]; a.x[t] = cpx<R>(); }
+    __syncthreads();
+    if (k > 0) {
+        if (!deflation_coeffs(a.rhs)) return;
+        for (int i = threadIdx.x; i < k; i += blockDim.x) t0[i] = tc[i];
         __syncthreads();
-        if (stop) return;
     }
+    project_g5(a.rhs);
+    if (!grid_norm2(a.rhs)) return;
+    if (threadIdx.x == 0) { bnorm = sqrt(h[0].x); stop = !(bnorm > 0) || !isfinite(bnorm); }
+    __syncthreads();
     const double tol_abs = a.tol * bnorm;
     int its = 0;
     bool have_x = false;
-    while (its < a.maxiter) {
-        // V0 = b - A x  (or b), beta = ||V0||
-        {
-            double acc = 0;
-            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-                cpx<R> r = a.b[t];
-                if ((t % (2 * a.ntv)) >= a.ntv) r = -r;    // gamma5^c r_c
-                if (have_x) r = r - coarse_row<R>(a, a.x, R(1), t);
-                a.V[t] = r;
-                acc += (double)r.re * r.re + (double)r.im * r.im;
-            }
-            block_partial(acc, 0.0, 0, wsum, nullptr);
-            flush(2 * (CG_MAXM + 2), 1);
-            if (!grid_sync(a.st, G, a.timeout)) return;
-            gather(2 * (CG_MAXM + 2), 1);
-            if (threadIdx.x == 0) {
-                beta = sqrt(h[0].x);
-                stop = !(beta > tol_abs) || !isfinite(beta);
-                if (!isfinite(beta)) atomicExch(&a.st->status, 2);
-                scale[0] = beta > 0 ? 1.0 / beta : 0.0;
-                g[0] = make_double2(beta, 0);
-                for (int i = 1; i <= CG_MAXM; ++i) g[i] = make_double2(0, 0);
-            }
-            __syncthreads();
-            if (stop) break;
+    while (!stop && its < a.maxiter) {
+        // V0 = rhs - op(x)  (or rhs)
+        if (have_x) {
+            if (!apply_op(a.x, R(1), a.V)) return;
+            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) a.V[t] = a.rhs[t] - a.V[t];
+        } else {
+            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) a.V[t] = a.rhs[t];
         }
+        __syncthreads();
+        if (!grid_norm2(a.V)) return;
+        if (threadIdx.x == 0) {
+            beta = sqrt(h[0].x);
+            stop = !(beta > tol_abs) || !isfinite(beta);
+            if (!isfinite(beta)) atomicExch(&a.st->status, 2);
+            scale[0] = beta > 0 ? 1.0 / beta : 0.0;
+            g[0] = make_double2(beta, 0);
+            for (int i = 1; i <= CG_MAXM; ++i) g[i] = make_double2(0, 0);
+        }
+        __syncthreads();
+        if (stop) break;
         const int mm = min(a.m, a.maxiter - its);
-        int k = 0;
+        int kk = 0;
         bool conv = false;
         for (int j = 0; j < mm; ++j) {
             cpx<R> *vj = a.V + (size_t)j * a.n;
             cpx<R> *w = a.V + (size_t)(j + 1) * a.n;
-            // w = A (s_j V_j) on owned rows; first Gram-Schmidt partials
-            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) w[t] = coarse_row<R>(a, vj, (R)scale[j], t);
+            if (!apply_op(vj, (R)scale[j], w)) return;
             for (int pass = 0; pass < 2; ++pass) {
                 for (int i = 0; i <= j; ++i) {
                     const cpx<R> *vi = a.V + (size_t)i * a.n;
@@ -226,19 +301,17 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
                         sr += (double)p.re * q.re + (double)p.im * q.im;
                         si += (double)p.re * q.im - (double)p.im * q.re;
                     }
-                    block_partial(sr * scale[i], si * scale[i], i, wsum, nullptr);
+                    warp_park(sr * scale[i], si * scale[i], i, wsum);
                 }
-                flush(pass * (CG_MAXM + 2), j + 1);
+                flush(pass == 0 ? OFF_H1 : OFF_H2, j + 1);
                 if (!grid_sync(a.st, G, a.timeout)) return;
-                gather(pass * (CG_MAXM + 2), j + 1);
+                gather(pass == 0 ? OFF_H1 : OFF_H2, j + 1);
                 if (threadIdx.x == 0) {
                     for (int i = 0; i <= j; ++i) {
                         double2 &col = Rm[j * (CG_MAXM + 1) + i];
-                        if (pass == 0) col = h[i];
-                        else col = make_double2(col.x + h[i].x, col.y + h[i].y);
+                        col = pass == 0 ? h[i] : make_double2(col.x + h[i].x, col.y + h[i].y);
                     }
                 }
-                // w -= sum_i h_i s_i V_i
                 for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
                     cpx<R> q = w[t];
                     for (int i = 0; i <= j; ++i) {
@@ -249,29 +322,15 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
                 }
                 __syncthreads();
             }
-            // norm of w
-            double acc = 0;
-            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-                cpx<R> q = w[t];
-                acc += (double)q.re * q.re + (double)q.im * q.im;
-            }
-            block_partial(acc, 0.0, 0, wsum, nullptr);
-            flush(2 * (CG_MAXM + 2), 1);
-            if (!grid_sync(a.st, G, a.timeout)) return;
-            gather(2 * (CG_MAXM + 2), 1);
+            if (!grid_norm2(w)) return;
             if (threadIdx.x == 0) {
                 const double nrm = sqrt(h[0].x);
                 double2 *col = Rm + j * (CG_MAXM + 1);
                 col[j + 1] = make_double2(nrm, 0);
-                // previous rotations
-                for (int i = 0; i < j; ++i) {
-                    double2 p = col[i], q = col[i + 1];
-                    double2 sv = sn[i];
-                    // p' = c p + s q ; q' = c q - conj(s) p
-                    double2 pn = make_double2(cs[i] * p.x + (sv.x * q.x - sv.y * q.y), cs[i] * p.y + (sv.x * q.y + sv.y * q.x));
-                    double2 qn = make_double2(cs[i] * q.x - (sv.x * p.x + sv.y * p.y), cs[i] * q.y - (sv.x * p.y - sv.y * p.x));
-                    col[i] = pn;
-                    col[i + 1] = qn;
+                for (int i = 0; i < j; ++i) {   // previous rotations
+                    double2 p = col[i], q = col[i + 1], sv = sn[i];
+                    col[i] = make_double2(cs[i] * p.x + (sv.x * q.x - sv.y * q.y), cs[i] * p.y + (sv.x * q.y + sv.y * q.x));
+                    col[i + 1] = make_double2(cs[i] * q.x - (sv.x * p.x + sv.y * p.y), cs[i] * q.y - (sv.x * p.y - sv.y * p.x));
                 }
                 double2 p = col[j], q = col[j + 1];
                 double ap = hypot(p.x, p.y), aq = hypot(q.x, q.y);
@@ -281,8 +340,7 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
                 else {
                     double tt = hypot(ap, aq);
                     c = ap / tt;
-                    // s = (p/|p|) conj(q) / t
-                    double ur = p.x / ap, ui = p.y / ap;
+                    double ur = p.x / ap, ui = p.y / ap;          // s = (p/|p|) conj(q) / t
                     sr = (ur * q.x + ui * q.y) / tt;
                     si = (ui * q.x - ur * q.y) / tt;
                 }
@@ -291,24 +349,21 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
                 col[j] = make_double2(c * p.x + (sr * q.x - si * q.y), c * p.y + (sr * q.y + si * q.x));
                 col[j + 1] = make_double2(0, 0);
                 double2 gj = g[j];
-                // g[j+1] = -conj(s) g[j] ; g[j] = c g[j]
                 g[j + 1] = make_double2(-(sr * gj.x + si * gj.y), -(sr * gj.y - si * gj.x));
                 g[j] = make_double2(c * gj.x, c * gj.y);
                 const double est = hypot(g[j + 1].x, g[j + 1].y);
                 if (!isfinite(nrm) || !isfinite(est)) atomicExch(&a.st->status, 2);
                 scale[j + 1] = nrm > 0 ? 1.0 / nrm : 0.0;
                 stop = (est <= tol_abs) || nrm == 0 || !isfinite(est);
-                kcols = j + 1;
             }
             __syncthreads();
-            k = j + 1;
+            kk = j + 1;
             if (stop) { conv = true; break; }
         }
-        // y = R^-1 g (thread 0), x += sum_i y_i s_i V_i
-        if (threadIdx.x == 0) {
-            for (int i = k - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) {   // y = R^-1 g
+            for (int i = kk - 1; i >= 0; --i) {
                 double2 sacc = g[i];
-                for (int l = i + 1; l < k; ++l) {
+                for (int l = i + 1; l < kk; ++l) {
                     double2 r = Rm[l * (CG_MAXM + 1) + i], yl = y[l];
                     sacc.x -= r.x * yl.x - r.y * yl.y;
                     sacc.y -= r.x * yl.y + r.y * yl.x;
@@ -322,25 +377,40 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
         __syncthreads();
         for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
             cpx<R> q = a.x[t];
-            for (int i = 0; i < k; ++i) {
+            for (int i = 0; i < kk; ++i) {
                 const cpx<R> yi((R)(y[i].x * scale[i]), (R)(y[i].y * scale[i]));
                 q = q + yi * a.V[(size_t)i * a.n + t];
             }
             a.x[t] = q;
         }
         have_x = true;
-        its += k;
-        // x must be complete before the next residual's matvec
-        if (!grid_sync(a.st, G, a.timeout)) return;
+        its += kk;
+        if (!grid_sync(a.st, G, a.timeout)) return;   // x complete before any matvec on it
         if (conv) break;
+        if (threadIdx.x == 0) stop = 0;
+        __syncthreads();
+    }
+    // e = y + W (t0 - E^-1 W^dag A y)
+    if (k > 0) {
+        cpx<R> *u = a.V;   // scratch
+        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) u[t] = qrow<R>(a, a.x, R(1), t);
+        __syncthreads();
+        if (!deflation_coeffs(u)) return;
+        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
+            cpx<R> q = a.x[t];
+            for (int i = 0; i < k; ++i) {
+                const cpx<R> ci((R)(t0[i].x - tc[i].x), (R)(t0[i].y - tc[i].y));
+                q = q + ci * a.W[(size_t)i * a.n + t];
+            }
+            a.x[t] = q;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.st->iters, its);
 }
 
-// Launch the persistent coarse GMRES for (Q_c - sigma) e_c = r_c (e_c from 0).
-// `state` points at a zero-initialised CGState (one reduction slot).
+// Launch the persistent coarse solve for (Q_c - sigma) e_c = r_c.
 template <typename R>
-void coarse_gmres_persistent(Ctx &c, double sigma, const void *rc, void *ec, DevBuf &Vbuf, DevBuf &pbuf, void *state) {
+void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, const void *rc, void *ec) {
     const int ntv = c.prm.n_tv;
     const int n = c.nagg * 2 * ntv;
     const int m = std::min(c.prm.coarse_restart, CG_MAXM);
@@ -351,8 +421,9 @@ void coarse_gmres_persistent(Ctx &c, double sigma, const void *rc, void *ec, Dev
     MG_REQUIRE(per_sm >= 1, MGEIG_ECUDA);
     int G = (n + CG_THREADS - 1) / CG_THREADS;
     G = std::max(1, std::min(G, dev_sms * per_sm));
-    Vbuf.alloc((size_t)(m + 1) * n * sizeof(cpx<R>));
-    pbuf.alloc((size_t)G * CG_SLOTS * sizeof(double2));
+    B.V->alloc((size_t)(m + 1) * n * sizeof(cpx<R>));
+    B.rhs->alloc((size_t)n * sizeof(cpx<R>));
+    B.partial->alloc((size_t)G * CG_SLOTS * sizeof(double2));
     CGArgs<R> a;
     a.nagg = c.nagg; a.ntv = ntv; a.n = n;
     for (int mu = 0; mu < 4; ++mu) a.cd[mu] = c.cdims[mu];
@@ -360,9 +431,15 @@ void coarse_gmres_persistent(Ctx &c, double sigma, const void *rc, void *ec, Dev
     a.sigma = (R)sigma;
     a.b = static_cast<const cpx<R> *>(rc);
     a.x = static_cast<cpx<R> *>(ec);
-    a.V = Vbuf.as<cpx<R>>();
-    a.partial = pbuf.as<double2>();
-    a.st = static_cast<CGState *>(state);
+    a.rhs = B.rhs->as<cpx<R>>();
+    a.V = B.V->as<cpx<R>>();
+    a.k = B.k;
+    MG_REQUIRE(a.k <= CG_MAXK, MGEIG_EINVAL);
+    a.W = static_cast<const cpx<R> *>(B.W);
+    a.AW = static_cast<const cpx<R> *>(B.AW);
+    a.Einv = static_cast<const double2 *>(B.Einv);
+    a.partial = B.partial->as<double2>();
+    a.st = static_cast<CGState *>(B.state);
     a.m = m;
     a.maxiter = c.prm.coarse_maxiter;
     a.tol = c.prm.coarse_tol;
@@ -372,7 +449,7 @@ void coarse_gmres_persistent(Ctx &c, double sigma, const void *rc, void *ec, Dev
     MG_CUDA(cudaLaunchCooperativeKernel((void *)coarse_gmres_kernel<R>, dim3(G), dim3(CG_THREADS), args, 0, c.stream));
 }
 
-template void coarse_gmres_persistent<float>(Ctx &, double, const void *, void *, DevBuf &, DevBuf &, void *);
-template void coarse_gmres_persistent<double>(Ctx &, double, const void *, void *, DevBuf &, DevBuf &, void *);
+template void coarse_gmres_persistent<float>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);
+template void coarse_gmres_persistent<double>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);
 
 }  // namespace mgeig

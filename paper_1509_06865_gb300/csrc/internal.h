@@ -128,8 +128,14 @@ template <typename R> void sap_sweep(Ctx &c, int colour, double sigma, const voi
 
 // ----- persistent coarse GMRES (coarse_gmres.cu) -----
 constexpr int COARSE_PERSISTENT_MAXM = 32;
+struct CoarseSolveBufs {
+    DevBuf *V, *rhs, *partial;   // basis, projected right-hand side, partial sums
+    void *state;                 // CGState (barrier, status, iteration counter)
+    int k;                       // deflation vectors (0: none)
+    const void *W, *AW, *Einv;   // k coarse vectors each; E^-1 (k x k complex double)
+};
 template <typename R>
-void coarse_gmres_persistent(Ctx &c, double sigma, const void *rc, void *ec, DevBuf &Vbuf, DevBuf &pbuf, void *state);
+void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, const void *rc, void *ec);
 
 // ----- the context -----
 struct Ctx {

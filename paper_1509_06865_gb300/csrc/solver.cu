@@ -145,9 +145,11 @@ struct Ctx::Work {
     DevBuf x64, t64, q64;        // FP64 temporaries
     DevBuf rR, zR, tR, eR;       // level-precision fine temporaries
     std::vector<DevBuf> S;       // GMRES smoother basis
-    std::vector<DevBuf> CV;      // coarse GMRES basis
     DevBuf rc, ec, ct;           // coarse vectors
-    DevBuf cgV, cgP;             // persistent coarse solver: basis, partial sums
+    DevBuf cgV, cgRhs, cgP;      // persistent coarse solver: basis, rhs, partial sums
+    DevBuf Wc, AWc, Edev, Einv;  // deflation: P^dag w_j, (Q_c - sigma) P^dag w_j, E, E^-1
+    bool defl_valid = false;
+    double defl_sigma = 0;
     std::vector<void *> W, P64, P;
 };
 
@@ -184,9 +186,10 @@ void mg_alloc(Ctx &c) {
         w.S.resize(w.smooth_k + 1);
         for (auto &b : w.S) b.alloc(fR_bytes(c));
     }
-    w.CV.resize(w.coarse_m + 1);
-    for (auto &b : w.CV) b.alloc(cR_bytes(c));
     w.rc.alloc(cR_bytes(c)); w.ec.alloc(cR_bytes(c)); w.ct.alloc(cR_bytes(c));
+    w.Wc.alloc(cR_bytes(c) * ntv); w.AWc.alloc(cR_bytes(c) * ntv);
+    w.Edev.alloc((size_t)ntv * ntv * sizeof(double2)); w.Einv.alloc((size_t)ntv * ntv * sizeof(double2));
+    w.defl_valid = false;
     c.Dc.alloc((size_t)9 * c.nagg * 4 * ntv * ntv * 2 * c.level_bytes());
 }
 
@@ -197,11 +200,11 @@ void mg_free(Ctx &c) {
     for (auto &b : w.V64) b.free();
     for (auto &b : w.Z) b.free();
     for (auto &b : w.S) b.free();
-    for (auto &b : w.CV) b.free();
     w.x64.free(); w.t64.free(); w.q64.free();
     w.rR.free(); w.zR.free(); w.tR.free(); w.eR.free();
     w.rc.free(); w.ec.free(); w.ct.free();
-    w.cgV.free(); w.cgP.free();
+    w.cgV.free(); w.cgRhs.free(); w.cgP.free();
+    w.Wc.free(); w.AWc.free(); w.Edev.free(); w.Einv.free();
     delete c.work;
     c.work = nullptr;
     c.Dc.free();
@@ -335,23 +338,87 @@ static int gmres(Ctx &c, Op op, const void *b, void *x, bool x_nonzero, size_t n
 // ---------------------------------------------------------------------------
 // the two-grid cycle
 
-// Coarse solve (Q_c - sigma) e = r_c.  GMRES runs on the equivalent system
-// (D_c - sigma gamma5^c) e = gamma5^c r_c (Q_c - sigma = gamma5^c (D_c - sigma
-// gamma5^c), Eq. 2.6 with a shift), whose spectrum lies in the right half plane
-// instead of around the origin.  One persistent cooperative launch when the
-// restart length fits it (the default), else the host-driven GMRES loop.
+// complex Gauss-Jordan inverse with partial pivoting (row-major n x n)
+static bool invert(int n, std::vector<cpx<double>> A, std::vector<cpx<double>> &inv) {
+    inv.assign((size_t)n * n, cpx<double>());
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = cpx<double>(1);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        double best = -1;
+        for (int r = col; r < n; ++r) {
+            cpx<double> z = A[(size_t)r * n + col];
+            double m = std::hypot(z.re, z.im);
+            if (m > best) { best = m; piv = r; }
+        }
+        if (!(best > 0) || !std::isfinite(best)) return false;
+        if (piv != col)
+            for (int k = 0; k < n; ++k) {
+                std::swap(A[(size_t)piv * n + k], A[(size_t)col * n + k]);
+                std::swap(inv[(size_t)piv * n + k], inv[(size_t)col * n + k]);
+            }
+        cpx<double> d = A[(size_t)col * n + col];
+        double dd = d.re * d.re + d.im * d.im;
+        cpx<double> di(d.re / dd, -d.im / dd);
+        for (int k = 0; k < n; ++k) {
+            A[(size_t)col * n + k] = A[(size_t)col * n + k] * di;
+            inv[(size_t)col * n + k] = inv[(size_t)col * n + k] * di;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            cpx<double> f = A[(size_t)r * n + col];
+            if (f.re == 0 && f.im == 0) continue;
+            for (int k = 0; k < n; ++k) {
+                A[(size_t)r * n + k] = A[(size_t)r * n + k] - f * A[(size_t)col * n + k];
+                inv[(size_t)r * n + k] = inv[(size_t)r * n + k] - f * inv[(size_t)col * n + k];
+            }
+        }
+    }
+    return true;
+}
+
+// (Q_c - sigma) W_c and E^-1 = (W_c^dag (Q_c - sigma) W_c)^-1 for the current
+// test vectors and shift (cached until the shift or P changes)
+template <typename R>
+static void deflation_prepare(Ctx &c, double sigma) {
+    Ctx::Work &w = *c.work;
+    if (!c.prm.coarse_deflate || (w.defl_valid && w.defl_sigma == sigma)) return;
+    const int k = c.prm.n_tv;
+    const size_t n = c.coarse_ncpx(), vb = cR_bytes(c);
+    std::vector<const void *> Wp(k);
+    for (int i = 0; i < k; ++i) Wp[i] = static_cast<const char *>(w.Wc.p) + vb * i;
+    for (int j = 0; j < k; ++j) {
+        void *awj = static_cast<char *>(w.AWc.p) + vb * j;
+        coarse_apply<R>(c, c.Dc.p, sigma, Wp[j], awj, false);
+        blas_multidot<R>(c, Wp.data(), k, awj, n, w.Edev.as<cpx<double>>() + (size_t)j * k);
+    }
+    std::vector<cpx<double>> Ecol((size_t)k * k), E((size_t)k * k), Ei;
+    MG_CUDA(cudaMemcpyAsync(Ecol.data(), w.Edev.p, Ecol.size() * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) E[(size_t)i * k + j] = Ecol[(size_t)j * k + i];   // E_ij = <W_i, A W_j>
+    MG_REQUIRE(invert(k, E, Ei), MGEIG_EBREAKDOWN);
+    MG_CUDA(cudaMemcpyAsync(w.Einv.p, Ei.data(), Ei.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+    sync(c);
+    w.defl_valid = true;
+    w.defl_sigma = sigma;
+}
+
+// Coarse solve (Q_c - sigma) e = r_c: one persistent cooperative launch (GMRES
+// on the deflated D_c form, see coarse_gmres.cu)
 template <typename R>
 static void coarse_solve(Ctx &c, double sigma, const void *rc, void *ec) {
     Ctx::Work &w = *c.work;
-    if (c.prm.coarse_restart <= COARSE_PERSISTENT_MAXM) {
-        coarse_gmres_persistent<R>(c, sigma, rc, ec, w.cgV, w.cgP, dslot(c, CGS));
-        return;
-    }
-    coarse_gamma5<R>(c, rc, w.ct.p);
-    auto op = [&](const void *x, void *y) { coarse_apply<R>(c, c.Dc.p, sigma, x, y, true); };
-    int its = gmres<R>(c, op, w.ct.p, ec, false, c.coarse_ncpx(), c.prm.coarse_tol, c.prm.coarse_restart,
-                       c.prm.coarse_maxiter, w.CV);
-    c.st.coarse_iters += its;
+    deflation_prepare<R>(c, sigma);
+    CoarseSolveBufs B;
+    B.V = &w.cgV;
+    B.rhs = &w.cgRhs;
+    B.partial = &w.cgP;
+    B.state = dslot(c, CGS);
+    B.k = c.prm.coarse_deflate ? c.prm.n_tv : 0;
+    B.W = w.Wc.p;
+    B.AW = w.AWc.p;
+    B.Einv = w.Einv.p;
+    coarse_gmres_persistent<R>(c, B, sigma, rc, ec);
 }
 
 // Adds the persistent coarse solver's iterations since the last call to the
@@ -405,13 +472,22 @@ static void mg_cycle(Ctx &c, double sigma, const void *r, void *z) {
 void mg_rebuild(Ctx &c) {
     Ctx::Work &w = *c.work;
     const int ntv = c.prm.n_tv;
+    const size_t vb = cR_bytes(c);
     build_interp<double>(c, (const void *const *)w.W.data(), ntv, w.P64.data());
     if (c.mixed()) {
         for (int j = 0; j < ntv; ++j) convert_f64_to_f32(c, w.P64[j], w.P[j], c.fine_ncpx());
         build_coarse<float>(c, (const void *const *)w.P.data(), c.Dc.p);
+        // coarse images P^dag w_j of the test vectors (the deflation space)
+        for (int j = 0; j < ntv; ++j) {
+            convert_f64_to_f32(c, w.W[j], w.rR.p, c.fine_ncpx());
+            restrict_vec<float>(c, (const void *const *)w.P.data(), w.rR.p, static_cast<char *>(w.Wc.p) + vb * j);
+        }
     } else {
         build_coarse<double>(c, (const void *const *)w.P.data(), c.Dc.p);
+        for (int j = 0; j < ntv; ++j)
+            restrict_vec<double>(c, (const void *const *)w.P.data(), w.W[j], static_cast<char *>(w.Wc.p) + vb * j);
     }
+    w.defl_valid = false;
 }
 
 // Gram-Schmidt (each step twice) of FP64 vectors v[0..n) in place

@@ -74,19 +74,20 @@ def test_sap_cycles(inputs, prec, tol):
     ctx.close()
 
 
-@pytest.mark.parametrize("smoother,restart", [(0, 30), (1, 30), (0, 40)],
-                         ids=["sap-persistent", "gmres-persistent", "sap-hostloop"])
+@pytest.mark.parametrize("smoother,deflate,restart", [(0, 1, 30), (1, 1, 30), (0, 0, 30), (0, 1, 5)],
+                         ids=["sap-deflated", "gmres-deflated", "sap-plain", "sap-deflated-restart5"])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-4)], ids=["fp64", "mixed"])
-def test_two_grid_cycle(inputs, smoother, restart, prec, tol):
-    """Coarse restart 30 runs the persistent cooperative coarse GMRES, 40 the
-    host-driven loop; both must reproduce the oracle's cycle."""
+def test_two_grid_cycle(inputs, smoother, deflate, restart, prec, tol):
+    """The persistent coarse solve with and without deflation of the test
+    vectors' coarse images, both smoothers, with and without restarts."""
     c, U, op, W, P, Dc = inputs
     params = dict(mg.DEFAULT_PARAMS, agg=c["agg"], sap_block=c["sap"], ntv=c["ntv"],
                   smoother="sap" if smoother == 0 else "gmres", coarse_tol=0.0, coarse_maxiter=12,
-                  coarse_restart=restart, sap_cycles=2, sap_mr_iters=3, smooth_steps=2, gmres_smooth_k=4)
+                  coarse_restart=restart, coarse_deflate=bool(deflate), sap_cycles=2, sap_mr_iters=3,
+                  smooth_steps=2, gmres_smooth_k=4)
     B = mg.TwoGrid(op, W, params)
-    ctx = make(c, prec, smoother, coarse_tol=0.0, coarse_maxiter=12, coarse_restart=restart, sap_cycles=2,
-               sap_mr_iters=3, smooth_steps=2, gmres_smooth_k=4)
+    ctx = make(c, prec, smoother, coarse_tol=0.0, coarse_maxiter=12, coarse_restart=restart,
+               coarse_deflate=deflate, sap_cycles=2, sap_mr_iters=3, smooth_steps=2, gmres_smooth_k=4)
     ctx.load_gauge(U)
     ctx.set_test_vectors(W)
     r = synth.gaussian_vectors(c["dims"], 1, 12)[0]
