@@ -38,8 +38,11 @@ COUNTS_FILE = os.path.join(ROOT, "bench_counts.json")
 
 
 def load_m0() -> float:
-    with open(os.path.join(ROOT, "tests", "golden", "config2_m0.json")) as f:
-        return float(json.load(f)["m0"])
+    with open(os.path.join(ROOT, "workloads.json")) as f:
+        m0 = json.load(f)["config2"]["m0"]
+    if m0 is None:
+        raise RuntimeError("workloads.json: config2 m0 not tuned yet")
+    return float(m0)
 
 
 def peaks():

@@ -100,6 +100,8 @@ typedef struct mgeig_params {
                              n_tv - n_eig); -1 = min(n_tv - n_eig, n_eig)       */
     int coarse_deflate;   /* 1: the coarse solve treats span{P^dag w_j} of the
                              test vectors exactly (Galerkin deflation), 0: plain */
+    int ritz_each_sweep;  /* 1: after every sweep of Algorithm 1 the iterated
+                             vectors become the Ritz vectors of Q in their span */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */

@@ -350,6 +350,7 @@ DEFAULT_PARAMS = dict(
     coarse_restart=30,
     coarse_maxiter=300,
     coarse_deflate=True,
+    ritz_each_sweep=True,
     outer_restart=20,
     outer_maxiter=200,
     solve_tol=1e-2,

@@ -24,6 +24,11 @@ Algorithm 1, per sweep over the unconverged i:
     lambda_i = <v_i|Q|v_i>,  eps_i = ||Q v_i - lambda_i v_i||
 starting from lambda_i = 0, eps_i = 1.  P is built from [v_1..v_N_eig] followed by
 the remaining test vectors when N_tv > N_eig.
+
+After every sweep (with ritz_each_sweep) the iterated vectors are replaced by the
+Ritz vectors of Q in their span, ordered by |theta| (lambda_i = theta_i,
+eps_i = ||Q v_i - theta_i v_i||).  Vector-wise RQI has no view of a cluster of
+nearly equal eigenvalues; the projection separates the vectors inside one.
 """
 from __future__ import annotations
 
@@ -87,6 +92,7 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
         n_eig: int, eps: float, params: dict, max_sweeps: int = 50, log=None):
     """Algorithm 1.  Returns (lambda, vectors, eps_i, stats), sorted by |lambda|."""
     p = params
+    ritz_each_sweep = p.get("ritz_each_sweep", True)
     V = [v.copy() for v in V[:n_eig]]
     lam = np.zeros(n_eig)
     res = np.ones(n_eig)
@@ -117,6 +123,12 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
             if log is not None:
                 log(f"sweep {stats['sweeps']} i={i} sigma={sigma:.6e} lambda={lam[i]:.12e} eps={res[i]:.3e} "
                     f"outer={info['iters']}")
+        if ritz_each_sweep:
+            R, _ = ritz_rotate(op, np.array(V))
+            V = [v for v in R]
+            for i in range(n_eig):
+                lam[i], res[i] = rayleigh(op, V[i])
+            rebuild()
     order = np.lexsort((lam, np.abs(lam)))
     return lam[order], np.array(V)[order], res[order], stats
 

@@ -30,7 +30,7 @@ class Params(C.Structure):
         ("setup_iters", C.c_int), ("outer_restart", C.c_int), ("outer_maxiter", C.c_int),
         ("coarse_restart", C.c_int), ("coarse_maxiter", C.c_int), ("coarse_tol", C.c_double),
         ("solve_tol", C.c_double), ("precision", C.c_int), ("smoother", C.c_int), ("max_sweeps", C.c_int),
-        ("n_guard", C.c_int), ("coarse_deflate", C.c_int),
+        ("n_guard", C.c_int), ("coarse_deflate", C.c_int), ("ritz_each_sweep", C.c_int),
     ]
 
 

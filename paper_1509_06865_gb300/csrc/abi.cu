@@ -50,6 +50,7 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (p.outer_restart < 1 || p.outer_restart > 100 || p.outer_maxiter < 1) return MGEIG_EINVAL;
     if (p.coarse_restart < 1 || p.coarse_restart > COARSE_PERSISTENT_MAXM || p.coarse_maxiter < 1) return MGEIG_EINVAL;
     if (p.coarse_deflate != 0 && p.coarse_deflate != 1) return MGEIG_EINVAL;
+    if (p.ritz_each_sweep != 0 && p.ritz_each_sweep != 1) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES) return MGEIG_EINVAL;
@@ -99,6 +100,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->max_sweeps = 50;
     p->n_guard = -1;
     p->coarse_deflate = 1;
+    p->ritz_each_sweep = 1;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {

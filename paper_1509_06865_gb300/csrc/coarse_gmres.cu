@@ -101,34 +101,52 @@ __device__ __forceinline__ cpx<double> ldcg(const cpx<double> *p) {
     return cpx<double>(v.x, v.y);
 }
 
-// row t of (Q_c - sigma)(s v) = (gamma5^c D_c - sigma)(s v)
+// u[t] = ((Q_c - sigma)(s v))[t] = ((gamma5^c D_c - sigma)(s v))[t] for the rows
+// t in [r0, r1); a group of TPR consecutive threads shares one row (its lanes
+// take the nine hop directions in turn) and reduces with shuffles.
+constexpr int TPR = 8;
+
 template <typename R>
-__device__ __forceinline__ cpx<R> qrow(const CGArgs<R> &a, const cpx<R> *v, R s, int t) {
+__device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *u, int r0, int r1) {
     const int n2 = 2 * a.ntv;
-    const int site = t / n2, row = t % n2;
-    int ac[4], rem = site;
-    for (int mu = 0; mu < 4; ++mu) { ac[mu] = rem % a.cd[mu]; rem /= a.cd[mu]; }
-    cpx<R> acc0, acc1;
-    for (int d = 0; d < 9; ++d) {
-        int nb = site;
-        if (d > 0) {
-            const int mu = (d - 1) / 2, step = (d & 1) ? 1 : -1;
-            int bc[4] = {ac[0], ac[1], ac[2], ac[3]};
-            bc[mu] = (bc[mu] + step + a.cd[mu]) % a.cd[mu];
-            nb = ((bc[3] * a.cd[2] + bc[2]) * a.cd[1] + bc[1]) * a.cd[0] + bc[0];
+    const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
+    for (int tb = r0; tb < r1; tb += ngrp) {
+        const int t = tb + grp;
+        cpx<R> acc0, acc1, acc2, acc3;
+        if (t < r1) {
+            const int site = t / n2, row = t % n2;
+            int ac[4], rem = site;
+            for (int mu = 0; mu < 4; ++mu) { ac[mu] = rem % a.cd[mu]; rem /= a.cd[mu]; }
+            for (int d = q; d < 9; d += TPR) {
+                int nb = site;
+                if (d > 0) {
+                    const int mu = (d - 1) / 2, step = (d & 1) ? 1 : -1;
+                    int bc[4] = {ac[0], ac[1], ac[2], ac[3]};
+                    bc[mu] = (bc[mu] + step + a.cd[mu]) % a.cd[mu];
+                    nb = ((bc[3] * a.cd[2] + bc[2]) * a.cd[1] + bc[1]) * a.cd[0] + bc[0];
+                }
+                const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
+                const cpx<R> *xb = v + (size_t)nb * n2;
+                int j = 0;
+                for (; j + 3 < n2; j += 4) {
+                    cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+                    cmac(acc1, blk[(size_t)(j + 1) * n2], ldcg(xb + j + 1));
+                    cmac(acc2, blk[(size_t)(j + 2) * n2], ldcg(xb + j + 2));
+                    cmac(acc3, blk[(size_t)(j + 3) * n2], ldcg(xb + j + 3));
+                }
+                for (; j < n2; ++j) cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+            }
         }
-        const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
-        const cpx<R> *xb = v + (size_t)nb * n2;
-        int j = 0;
-        for (; j + 1 < n2; j += 2) {
-            cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
-            cmac(acc1, blk[(size_t)(j + 1) * n2], ldcg(xb + j + 1));
+        cpx<R> acc = (acc0 + acc1) + (acc2 + acc3);
+        for (int o = 1; o < TPR; o <<= 1) {
+            acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+            acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
         }
-        if (j < n2) cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+        if (t < r1 && q == 0) {
+            if ((t % n2) >= a.ntv) acc = -acc;
+            u[t] = s * acc - (a.sigma * s) * ldcg(v + t);
+        }
     }
-    cpx<R> acc = acc0 + acc1;
-    if (row >= a.ntv) acc = -acc;
-    return s * acc - (a.sigma * s) * ldcg(v + t);
 }
 
 template <typename R>
@@ -230,7 +248,7 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
     };
     // u = gamma5^c Pi (Q_c - sigma)(s v) on the owned rows
     auto apply_op = [&](const cpx<R> *v, R s, cpx<R> *u) -> bool {
-        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) u[t] = qrow<R>(a, v, s, t);
+        qmatvec<R>(a, v, s, u, r0, r1);
         __syncthreads();
         if (k > 0 && !deflation_coeffs(u)) return false;
         project_g5(u);
@@ -393,7 +411,7 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
     // e = y + W (t0 - E^-1 W^dag A y)
     if (k > 0) {
         cpx<R> *u = a.V;   // scratch
-        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) u[t] = qrow<R>(a, a.x, R(1), t);
+        qmatvec<R>(a, a.x, R(1), u, r0, r1);
         __syncthreads();
         if (!deflation_coeffs(u)) return;
         for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
@@ -419,8 +437,8 @@ void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, con
     int per_sm = 0;
     MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel<R>, CG_THREADS, 0));
     MG_REQUIRE(per_sm >= 1, MGEIG_ECUDA);
-    int G = (n + CG_THREADS - 1) / CG_THREADS;
-    G = std::max(1, std::min(G, dev_sms * per_sm));
+    int G = (n * TPR + CG_THREADS - 1) / CG_THREADS;
+    G = std::max(1, std::min(G, std::min(dev_sms * per_sm, 2 * dev_sms)));
     B.V->alloc((size_t)(m + 1) * n * sizeof(cpx<R>));
     B.rhs->alloc((size_t)n * sizeof(cpx<R>));
     B.partial->alloc((size_t)G * CG_SLOTS * sizeof(double2));

@@ -79,7 +79,12 @@ __device__ __forceinline__ int neighbor(const Geom &g, int s, const int c[4], in
 
 template <typename R> struct Spinor;
 
+// Spinor<R>::comp(p, V, k, s): component k of site s as a complex lvalue
+// (FP64 [12][V] complex; FP32 [6][V] float4 = [6][V][2] complex).
 template <> struct Spinor<double> {
+    __device__ __forceinline__ static cpx<double> &comp(const cpx<double> *p, int V, int k, int s) {
+        return const_cast<cpx<double> *>(p)[(size_t)k * V + s];
+    }
     __device__ __forceinline__ static void load(const void *base, int V, int s, cpx<double> v[12]) {
         const double2 *p = static_cast<const double2 *>(base);
 #pragma unroll
@@ -93,6 +98,9 @@ template <> struct Spinor<double> {
 };
 
 template <> struct Spinor<float> {
+    __device__ __forceinline__ static cpx<float> &comp(const cpx<float> *p, int V, int k, int s) {
+        return const_cast<cpx<float> *>(p)[((size_t)(k >> 1) * V + s) * 2 + (k & 1)];
+    }
     __device__ __forceinline__ static void load(const void *base, int V, int s, cpx<float> v[12]) {
         const float4 *p = static_cast<const float4 *>(base);
 #pragma unroll

@@ -63,88 +63,95 @@ struct PtrList { const void *p[24]; };
 struct MutPtrList { void *p[24]; };
 
 // ---------------------------------------------------------------------------
-// interpolation: Gram-Schmidt per (aggregate, chirality) in FP64
+// interpolation: classical Gram-Schmidt (twice) per (aggregate, chirality),
+// arithmetic in precision R (FP64 for the all-FP64 path; FP32 for the mixed
+// path, whose P is stored in FP32).  Test vectors are read in FP64.  One CTA per
+// (aggregate, chirality); all <q_i, w> of one pass share one block reduction.
 
 constexpr int PB_THREADS = 256;
-constexpr int PB_MAXS = 4;   // sites per thread (aggregates of up to 1024 sites)
+constexpr int PB_MAXS = 4;    // sites per thread (aggregates of up to 1024 sites)
+constexpr int PB_MAXN = 24;   // test vectors
 
-__device__ __forceinline__ double2 block_sum2(double a, double b, double *sh) {
-    // sh: 2 * 32 doubles
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    __syncthreads();
-    if (lane == 0) { sh[2 * w] = a; sh[2 * w + 1] = b; }
-    __syncthreads();
-    double x = 0, y = 0;
-    for (int i = 0; i < nw; ++i) { x += sh[2 * i]; y += sh[2 * i + 1]; }
-    return make_double2(x, y);
-}
-
+template <typename R>
 __global__ void __launch_bounds__(PB_THREADS) interp_kernel(Geom g, AggGeom A, PtrList W, int ntv, MutPtrList P) {
-    __shared__ double sh[64];
+    __shared__ double sh[PB_THREADS / 32][2 * PB_MAXN];
+    __shared__ double hs[2 * PB_MAXN];
     const int a = blockIdx.x >> 1, chir = blockIdx.x & 1;
     const int V = g.V;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     int sites[PB_MAXS];
     int ns = 0;
     for (int l = threadIdx.x; l < A.vol && ns < PB_MAXS; l += blockDim.x) {
         int lc[4];
         sites[ns++] = agg_site(g, A, a, l, lc);
     }
+    // block-reduce cnt complex values parked per warp in sh -> hs (all threads)
+    auto reduce = [&](int cnt) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * cnt; i += blockDim.x) {
+            double s = 0;
+            for (int w = 0; w < nw; ++w) s += sh[w][i];
+            hs[i] = s;
+        }
+        __syncthreads();
+    };
+    auto warp_sum = [&](double v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
     for (int j = 0; j < ntv; ++j) {
-        cpx<double> w[PB_MAXS][6];
+        cpx<R> w[PB_MAXS][6];
         const double2 *src = static_cast<const double2 *>(W.p[j]);
         for (int i = 0; i < PB_MAXS; ++i)
             for (int k = 0; k < 6; ++k) {
-                if (i < ns) { double2 t = src[(size_t)(chir * 6 + k) * V + sites[i]]; w[i][k] = cpx<double>(t.x, t.y); }
-                else w[i][k] = cpx<double>();
+                if (i < ns) { double2 t = src[(size_t)(chir * 6 + k) * V + sites[i]]; w[i][k] = cpx<R>((R)t.x, (R)t.y); }
+                else w[i][k] = cpx<R>();
             }
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int pass = 0; pass < 2 && j > 0; ++pass) {
             for (int q = 0; q < j; ++q) {
-                const double2 *pq = static_cast<const double2 *>(P.p[q]);
-                cpx<double> d;
+                const cpx<R> *pq = static_cast<const cpx<R> *>(P.p[q]);
+                cpx<R> d;
                 for (int i = 0; i < ns; ++i)
-                    for (int k = 0; k < 6; ++k) {
-                        double2 t = pq[(size_t)(chir * 6 + k) * V + sites[i]];
-                        cmac_conj(d, cpx<double>(t.x, t.y), w[i][k]);
-                    }
-                double2 h = block_sum2(d.re, d.im, sh);
-                cpx<double> hc(h.x, h.y);
+                    for (int k = 0; k < 6; ++k) cmac_conj(d, Spinor<R>::comp(pq, V, chir * 6 + k, sites[i]), w[i][k]);
+                const double re = warp_sum((double)d.re), im = warp_sum((double)d.im);
+                if (lane == 0) { sh[wp][2 * q] = re; sh[wp][2 * q + 1] = im; }
+            }
+            reduce(j);
+            for (int q = 0; q < j; ++q) {
+                const cpx<R> *pq = static_cast<const cpx<R> *>(P.p[q]);
+                const cpx<R> hc((R)hs[2 * q], (R)hs[2 * q + 1]);
                 for (int i = 0; i < ns; ++i)
-                    for (int k = 0; k < 6; ++k) {
-                        double2 t = pq[(size_t)(chir * 6 + k) * V + sites[i]];
-                        w[i][k] = w[i][k] - hc * cpx<double>(t.x, t.y);
-                    }
+                    for (int k = 0; k < 6; ++k) w[i][k] = w[i][k] - hc * Spinor<R>::comp(pq, V, chir * 6 + k, sites[i]);
             }
         }
         double nn = 0;
         for (int i = 0; i < ns; ++i)
-            for (int k = 0; k < 6; ++k) nn += w[i][k].re * w[i][k].re + w[i][k].im * w[i][k].im;
-        double2 tot = block_sum2(nn, 0.0, sh);
-        const double inv = tot.x > 0 ? 1.0 / sqrt(tot.x) : 0.0;
-        double2 *dst = static_cast<double2 *>(P.p[j]);
+            for (int k = 0; k < 6; ++k) nn += (double)w[i][k].re * w[i][k].re + (double)w[i][k].im * w[i][k].im;
+        nn = warp_sum(nn);
+        if (lane == 0) { sh[wp][0] = nn; sh[wp][1] = 0; }
+        reduce(1);
+        const R inv = hs[0] > 0 ? (R)(1.0 / sqrt(hs[0])) : R(0);
+        cpx<R> *dst = static_cast<cpx<R> *>(P.p[j]);
         for (int i = 0; i < ns; ++i)
-            for (int k = 0; k < 6; ++k)
-                dst[(size_t)(chir * 6 + k) * V + sites[i]] = make_double2(w[i][k].re * inv, w[i][k].im * inv);
+            for (int k = 0; k < 6; ++k) Spinor<R>::comp(dst, V, chir * 6 + k, sites[i]) = inv * w[i][k];
     }
 }
 
-// P64 (FP64 spinors) -> P in precision R
+// P (ntv spinors of precision R) from the FP64 test vectors W64
 template <typename R>
 void build_interp(Ctx &c, const void *const *W64, int ntv, void *const *P) {
     AggGeom A = make_agg(c, c.prm.agg);
-    MG_REQUIRE(A.vol <= PB_THREADS * PB_MAXS, MGEIG_EINVAL);
+    MG_REQUIRE(A.vol <= PB_THREADS * PB_MAXS && ntv <= PB_MAXN, MGEIG_EINVAL);
     PtrList w{};
     MutPtrList p{};
     for (int j = 0; j < ntv; ++j) { w.p[j] = W64[j]; p.p[j] = P[j]; }
     const int threads = A.vol < PB_THREADS ? ((A.vol + 31) / 32) * 32 : PB_THREADS;
-    TimeScope ts(c.timer, K_PBUILD, (double)ntv * c.g.V * 12 * 32);
-    interp_kernel<<<A.n * 2, threads, 0, c.stream>>>(c.g, A, w, ntv, p);
+    TimeScope ts(c.timer, K_PBUILD, (double)ntv * c.g.V * 12 * (16 + 2 * sizeof(R)));
+    interp_kernel<R><<<A.n * 2, threads, 0, c.stream>>>(c.g, A, w, ntv, p);
     MG_CHECK_LAUNCH();
 }
 template void build_interp<double>(Ctx &, const void *const *, int, void *const *);
+template void build_interp<float>(Ctx &, const void *const *, int, void *const *);
 
 // ---------------------------------------------------------------------------
 // restriction r_c = P^dag r
@@ -447,12 +454,20 @@ void coarse_apply(Ctx &c, const void *Dc, double sigma, const void *x, void *y, 
 // ---------------------------------------------------------------------------
 // SAP: one colour of blocks; CTA = one block, thread = one site
 
+// FP32: the block's forward links (two rows, 3 float4 per link) are staged in
+// shared memory once and serve every MR step (the backward link of an in-block
+// hop is the forward link of the in-block neighbour); two CTAs fit an SM.
+template <typename R> struct SapBounds { static constexpr int minb = 1; };
+template <> struct SapBounds<float> { static constexpr int minb = 2; };
+
 template <typename R>
-__global__ void sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
-                           const void *__restrict__ clov, const void *__restrict__ rhs, int rhs_g5, void *z,
-                           int mr_iters) {
+__global__ void __launch_bounds__(256, SapBounds<R>::minb)
+sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
+           const void *__restrict__ clov, const void *__restrict__ rhs, int rhs_g5, void *z, int mr_iters) {
     extern __shared__ unsigned char smem_raw[];
     cpx<R> *rho = reinterpret_cast<cpx<R> *>(smem_raw);       // [vol][12]
+    float4 *slink = reinterpret_cast<float4 *>(smem_raw + (size_t)B.vol * 12 * sizeof(cpx<R>));   // [vol][4][3]
+    constexpr bool stage = sizeof(R) == 4;
     __shared__ double red[3 * 32];
     const int b = blockIdx.x;
     {
@@ -471,6 +486,11 @@ __global__ void sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *_
     cpx<R> e[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) e[k] = cpx<R>();
+    if (stage && active) {
+        const float4 *ug = static_cast<const float4 *>(U);
+        for (int mu = 0; mu < 4; ++mu)
+            for (int e = 0; e < 3; ++e) slink[(l * 4 + mu) * 3 + e] = ug[((size_t)mu * 3 + e) * V + s];
+    }
     // residual of D_sigma z = rhs on this block (z read with its global neighbours)
     if (active) {
         cpx<R> up[6], lo[6];
@@ -519,10 +539,20 @@ __global__ void sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *_
                     if (lm < 0 || lm >= B.agg[mu]) continue;
                     int ln = l + (fwd ? 1 : -1) * (mu == 0 ? 1 : mu == 1 ? B.agg[0] : mu == 2 ? B.agg[0] * B.agg[1]
                                                                                               : B.agg[0] * B.agg[1] * B.agg[2]);
-                    int ph;
-                    const int n = neighbor(g, s, c, mu, fwd, &ph);
                     cpx<R> u[9], psi[12];
-                    Gauge<R>::load(U, V, mu, fwd ? s : n, u);
+                    if constexpr (stage) {
+                        const float4 *q = slink + ((fwd ? l : ln) * 4 + mu) * 3;
+                        const float4 a = q[0], b = q[1], cc = q[2];
+                        u[0] = cpx<R>(a.x, a.y); u[1] = cpx<R>(a.z, a.w); u[2] = cpx<R>(b.x, b.y);
+                        u[3] = cpx<R>(b.z, b.w); u[4] = cpx<R>(cc.x, cc.y); u[5] = cpx<R>(cc.z, cc.w);
+                        u[6] = conj(u[1] * u[5] - u[2] * u[4]);
+                        u[7] = conj(u[2] * u[3] - u[0] * u[5]);
+                        u[8] = conj(u[0] * u[4] - u[1] * u[3]);
+                    } else {
+                        int ph;
+                        const int n = neighbor(g, s, c, mu, fwd, &ph);
+                        Gauge<R>::load(U, V, mu, fwd ? s : n, u);
+                    }
 #pragma unroll
                     for (int k = 0; k < 12; ++k) psi[k] = rho[ln * 12 + k];
                     hop_accumulate<R>(mu, fwd, u, psi, (R)1, up, lo);
@@ -577,7 +607,7 @@ void sap_sweep(Ctx &c, int colour, double sigma, const void *rhs, bool rhs_gamma
     AggGeom B = make_agg(c, c.prm.sap_block);
     MG_REQUIRE(B.vol <= 1024, MGEIG_EINVAL);
     const int threads = ((B.vol + 31) / 32) * 32;
-    const size_t smem = (size_t)B.vol * 12 * sizeof(cpx<R>);
+    const size_t smem = (size_t)B.vol * 12 * sizeof(cpx<R>) + (sizeof(R) == 4 ? (size_t)B.vol * 12 * sizeof(float4) : 0);
     MG_CUDA(cudaFuncSetAttribute(sap_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const void *U = sizeof(R) == 8 ? c.U64.p : c.U32.p;
     const void *C = sizeof(R) == 8 ? c.clov64.p : c.clov32.p;

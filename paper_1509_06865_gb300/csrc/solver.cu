@@ -13,9 +13,20 @@
 #include <algorithm>
 #include <numeric>
 
+#include <cstdlib>
+
 #include "internal.h"
 
 namespace mgeig {
+
+// Progress log on stderr when the environment variable MGEIG_LOG is set.
+static bool log_on() {
+    static const bool on = std::getenv("MGEIG_LOG") != nullptr;
+    return on;
+}
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 // ---------------------------------------------------------------------------
 // device buffers, timer
@@ -473,9 +484,8 @@ void mg_rebuild(Ctx &c) {
     Ctx::Work &w = *c.work;
     const int ntv = c.prm.n_tv;
     const size_t vb = cR_bytes(c);
-    build_interp<double>(c, (const void *const *)w.W.data(), ntv, w.P64.data());
     if (c.mixed()) {
-        for (int j = 0; j < ntv; ++j) convert_f64_to_f32(c, w.P64[j], w.P[j], c.fine_ncpx());
+        build_interp<float>(c, (const void *const *)w.W.data(), ntv, w.P.data());
         build_coarse<float>(c, (const void *const *)w.P.data(), c.Dc.p);
         // coarse images P^dag w_j of the test vectors (the deflation space)
         for (int j = 0; j < ntv; ++j) {
@@ -483,6 +493,7 @@ void mg_rebuild(Ctx &c) {
             restrict_vec<float>(c, (const void *const *)w.P.data(), w.rR.p, static_cast<char *>(w.Wc.p) + vb * j);
         }
     } else {
+        build_interp<double>(c, (const void *const *)w.W.data(), ntv, w.P64.data());
         build_coarse<double>(c, (const void *const *)w.P.data(), c.Dc.p);
         for (int j = 0; j < ntv; ++j)
             restrict_vec<double>(c, (const void *const *)w.P.data(), w.W[j], static_cast<char *>(w.Wc.p) + vb * j);
@@ -552,12 +563,18 @@ static void setup_impl(Ctx &c, uint64_t seed) {
     orthonormalise(c, w.W, ntv);
     mg_rebuild(c);
     for (int it = 0; it < c.prm.setup_iters; ++it) {
+        const double t0 = now_s();
         for (int j = 0; j < ntv; ++j) {
             mg_cycle_f64<R>(c, 0.0, w.W[j], w.t64.p);
             blas_copy<double>(c, w.t64.p, w.W[j], c.fine_ncpx());
         }
         orthonormalise(c, w.W, ntv);
         mg_rebuild(c);
+        if (log_on()) {
+            const long long ci = c.st.coarse_iters;
+            coarse_iters_take(c);
+            fprintf(stderr, "mgeig setup iter %d coarse %lld %.3fs\n", it, c.st.coarse_iters - ci, now_s() - t0);
+        }
     }
     sync(c);
 }
@@ -683,13 +700,13 @@ static void herm_eig(int n, std::vector<cpx<double>> A, std::vector<double> &w, 
     for (int i = 0; i < n; ++i) w[i] = a(i, i).re;
 }
 
-// Ritz vectors of Q in span(W), ordered by |theta| then theta
-static void ritz_rotate(Ctx &c) {
+// Ritz vectors of Q in span(W[0..n)), ordered by |theta| then theta, written
+// back into W[0..n).  Scratch: the P64 and RR vector sets (P is rebuilt after).
+static void ritz_rotate(Ctx &c, int n) {
     Ctx::Work &w = *c.work;
-    const int n = c.prm.n_tv;
     const size_t N = c.fine_ncpx();
     std::vector<cpx<double>> H((size_t)n * n);
-    std::vector<const void *> X(w.W.begin(), w.W.end());
+    std::vector<const void *> X(w.W.begin(), w.W.begin() + n);
     for (int j = 0; j < n; ++j) {
         apply_fine<double>(c, MODE_QSIGMA, 0.0, w.W[j], w.q64.p);
         blas_multidot<double>(c, X.data(), n, w.q64.p, N, dslot(c, H1));
@@ -711,7 +728,6 @@ static void ritz_rotate(Ctx &c) {
         double fa = std::fabs(th[a]), fb = std::fabs(th[b]);
         return fa != fb ? fa < fb : th[a] < th[b];
     });
-    // new vectors into the P64 area (scratch here), then copy back
     for (int k = 0; k < n; ++k) {
         std::vector<cpx<double>> coef(n);
         for (int i = 0; i < n; ++i) coef[i] = Y[(size_t)i * n + ord[k]];
@@ -742,7 +758,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
     const int spare = c.prm.n_tv - n_want;
     const int guard = c.prm.n_guard < 0 ? std::min(spare, n_want) : std::min(spare, c.prm.n_guard);
     const int n_eig = n_want + guard;
-    ritz_rotate(c);
+    ritz_rotate(c, c.prm.n_tv);
     mg_rebuild(c);
     std::vector<double> lam(n_eig, 0.0), eps(n_eig, 1.0);
     int sweeps = 0;
@@ -757,6 +773,8 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
         for (int i = 0; i < n_eig; ++i) {
             if (eps[i] <= tol) continue;
             const double sigma = lam[i] * std::max(1.0 - eps[i], 0.0);
+            const double t0 = now_s();
+            const int outer0 = c.st.outer_iters;
             int rc = fgmres_solve(c, sigma, w.W[i], w.x64.p, c.prm.solve_tol);
             if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
             if (i > 0) {
@@ -776,6 +794,28 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             auto le = rayleigh(c, w.W[i]);
             lam[i] = le.first;
             eps[i] = le.second;
+            if (log_on()) {
+                const long long ci = c.st.coarse_iters;
+                coarse_iters_take(c);
+                fprintf(stderr, "mgeig rqi sweep %d i %d sigma %.6e lambda %.12e eps %.3e outer %d coarse %lld %s %.3fs\n",
+                        sweeps, i, sigma, lam[i], eps[i], c.st.outer_iters - outer0, c.st.coarse_iters - ci,
+                        rc == MGEIG_OK ? "ok" : "cap", now_s() - t0);
+            }
+        }
+        if (c.prm.ritz_each_sweep) {
+            // Rayleigh-Ritz on the iterated vectors: separates nearly equal eigenvalues
+            ritz_rotate(c, n_eig);
+            for (int i = 0; i < n_eig; ++i) {
+                auto le = rayleigh(c, w.W[i]);
+                lam[i] = le.first;
+                eps[i] = le.second;
+            }
+            mg_rebuild(c);
+            if (log_on()) {
+                double mx = 0;
+                for (int i = 0; i < n_eig; ++i) mx = std::max(mx, eps[i]);
+                fprintf(stderr, "mgeig rqi sweep %d rayleigh-ritz max eps %.3e\n", sweeps, mx);
+            }
         }
     }
     c.st.sweeps = sweeps;
@@ -935,8 +975,10 @@ void coarse_op_f64(Ctx &c, void *out64) {
 
 void interp_f64(Ctx &c, void *const *out64) {
     Ctx::Work &w = *c.work;
-    for (int j = 0; j < c.prm.n_tv; ++j)
-        MG_CUDA(cudaMemcpyAsync(out64[j], w.P64[j], f64_bytes(c), cudaMemcpyDeviceToDevice, c.stream));
+    for (int j = 0; j < c.prm.n_tv; ++j) {
+        if (c.mixed()) convert_f32_to_f64(c, w.P[j], out64[j], c.fine_ncpx());
+        else MG_CUDA(cudaMemcpyAsync(out64[j], w.P64[j], f64_bytes(c), cudaMemcpyDeviceToDevice, c.stream));
+    }
 }
 
 }  // namespace mgeig

@@ -48,7 +48,7 @@ def test_interp_restrict_prolong_coarse(inputs, prec, tol):
     ctx = make(c, prec)
     ctx.load_gauge(U)
     ctx.set_test_vectors(W)
-    assert rel_err(ctx.get_interp(), P.vectors()) < 1e-12      # P is always built in FP64
+    assert rel_err(ctx.get_interp(), P.vectors()) < (1e-12 if prec == 0 else 2e-6)
     r = synth.gaussian_vectors(c["dims"], 1, 3)[0]
     assert rel_err(ctx.restrict(r), P.restrict(r)) < tol
     ec = P.restrict(synth.gaussian_vectors(c["dims"], 1, 4)[0])
