@@ -355,5 +355,5 @@ DEFAULT_PARAMS = dict(
     outer_maxiter=200,
     solve_tol=1e-2,
     setup_smooth=3,
-    setup_iters=6,
+    setup_iters=10,
 )

@@ -88,7 +88,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->smooth_steps = 2;
     p->gmres_smooth_k = 8;
     p->setup_smooth = 3;
-    p->setup_iters = 6;
+    p->setup_iters = 10;
     p->outer_restart = 20;
     p->outer_maxiter = 200;
     p->coarse_restart = 30;
