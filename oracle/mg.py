@@ -319,7 +319,13 @@ class TwoGrid:
             t = coeff(u)
             return u - sum(ti * awi for ti, awi in zip(t, AW))
 
-        y, _ = krylov.gmres(lambda v: C.gamma5(project(C.apply(v, sigma))), C.gamma5(project(rc)), **gm)
+        rhs = C.gamma5(project(rc))
+        # the tolerance refers to ||r_c||: a right-hand side lying mostly in span(W)
+        # leaves a tiny projected system that needs no further reduction
+        rn = np.linalg.norm(rhs)
+        gm["tol"] = gm["tol"] * np.linalg.norm(rc) / rn if rn > 0 else 0.0
+        y = np.zeros_like(rc) if rn == 0 else krylov.gmres(
+            lambda v: C.gamma5(project(C.apply(v, sigma))), rhs, **gm)[0]
         t0 = coeff(rc)
         t1 = coeff(C.apply(y, sigma))
         return y + sum((a - b) * w for a, b, w in zip(t0, t1, Wc))

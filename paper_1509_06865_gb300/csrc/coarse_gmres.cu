@@ -29,7 +29,7 @@
 
 namespace mgeig {
 
-constexpr int CG_THREADS = 256;
+constexpr int CG_THREADS = 1024;
 constexpr int CG_MAXM = COARSE_PERSISTENT_MAXM;   // restart length limit
 constexpr int CG_MAXK = 24;                       // deflation vectors (= max N_tv)
 constexpr int OFF_H1 = 0, OFF_H2 = CG_MAXM + 2, OFF_N = 2 * (CG_MAXM + 2), OFF_P = OFF_N + 2;
@@ -164,7 +164,7 @@ __device__ __forceinline__ void warp_park(double re, double im, int i, double2 *
 }
 
 template <typename R>
-__global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
+__global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a) {
     __shared__ double2 wsum[(CG_THREADS / 32) * WS];
     __shared__ double2 h[WS];
     __shared__ double2 Rm[(CG_MAXM + 1) * CG_MAXM];   // rotated Hessenberg, column-major
@@ -195,15 +195,22 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
             mypart[off + i] = make_double2(sr, si);
         }
     };
-    // after a barrier: h[i] = sum over blocks of partial[.][off + i]
+    // after a barrier: h[i] = sum over blocks of partial[.][off + i]; warp i
+    // reads the G partials of value i (lanes stride over the blocks) and
+    // reduces them in a fixed order
     auto gather = [&](int off, int cnt) {
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int lane = threadIdx.x & 31;
+        for (int i = threadIdx.x >> 5; i < cnt; i += nw) {
             double sr = 0, si = 0;
-            for (unsigned int q = 0; q < G; ++q) {
+            for (unsigned int q = lane; q < G; q += 32) {
                 double2 p = __ldcg(a.partial + (size_t)q * CG_SLOTS + off + i);
                 sr += p.x; si += p.y;
             }
-            h[i] = make_double2(sr, si);
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) h[i] = make_double2(sr, si);
         }
         __syncthreads();
     };
@@ -268,8 +275,13 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
         return true;
     };
 
-    // rhs = gamma5^c Pi r_c, t0 = E^-1 W^dag r_c, x = 0
+    // rhs = gamma5^c Pi r_c, t0 = E^-1 W^dag r_c, x = 0.  The tolerance refers
+    // to ||r_c||: when r_c lies mostly in span(W) the projected right-hand side
+    // is tiny and needs no further reduction.
     for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) { a.rhs[t] = a.b[t]; a.x[t] = cpx<R>(); }
+    __syncthreads();
+    if (!grid_norm2(a.rhs)) return;
+    if (threadIdx.x == 0) bnorm = sqrt(h[0].x);
     __syncthreads();
     if (k > 0) {
         if (!deflation_coeffs(a.rhs)) return;
@@ -277,8 +289,7 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_gmres_kernel(CGArgs<R> a) {
         __syncthreads();
     }
     project_g5(a.rhs);
-    if (!grid_norm2(a.rhs)) return;
-    if (threadIdx.x == 0) { bnorm = sqrt(h[0].x); stop = !(bnorm > 0) || !isfinite(bnorm); }
+    if (threadIdx.x == 0) stop = !(bnorm > 0) || !isfinite(bnorm);
     __syncthreads();
     const double tol_abs = a.tol * bnorm;
     int its = 0;
@@ -438,7 +449,7 @@ void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, con
     MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel<R>, CG_THREADS, 0));
     MG_REQUIRE(per_sm >= 1, MGEIG_ECUDA);
     int G = (n * TPR + CG_THREADS - 1) / CG_THREADS;
-    G = std::max(1, std::min(G, std::min(dev_sms * per_sm, 2 * dev_sms)));
+    G = std::max(1, std::min(G, std::min(dev_sms * per_sm, dev_sms)));
     B.V->alloc((size_t)(m + 1) * n * sizeof(cpx<R>));
     B.rhs->alloc((size_t)n * sizeof(cpx<R>));
     B.partial->alloc((size_t)G * CG_SLOTS * sizeof(double2));
