@@ -96,10 +96,11 @@ typedef struct mgeig_params {
     int precision;        /* MGEIG_FP64 or MGEIG_MIXED                          */
     int smoother;         /* MGEIG_SAP or MGEIG_GMRES                           */
     int max_sweeps;       /* Rayleigh quotient iteration: sweep cap             */
-    int n_guard;          /* extra iterated vectors beyond n_eig (capped at
-                             n_tv - n_eig); -1 = min(n_tv - n_eig, n_eig)       */
-    int coarse_deflate;   /* 1: the coarse solve treats span{P^dag w_j} of the
-                             test vectors exactly (Galerkin deflation), 0: plain */
+    int n_guard;          /* extra iterated vectors beyond n_eig (n_eig + n_guard
+                             <= 64); -1 = max(n_eig, n_tv)                      */
+    int coarse_deflate;   /* 1: outside the setup the coarse solve treats
+                             span{P^dag w_j} of the test vectors exactly (Galerkin
+                             deflation), 0: plain                               */
     int ritz_each_sweep;  /* 1: after every sweep of Algorithm 1 the iterated
                              vectors become the Ritz vectors of Q in their span */
 } mgeig_params;
@@ -224,7 +225,10 @@ int mgeig_solve(mgeig_ctx *ctx, double sigma, const double *b, double *x, double
  * Sec. 2.1 after Algorithm 1).  Needs mgeig_setup.
  * Outputs (any may be NULL): evals[n_eig], evecs[n_eig host spinors, unit norm,
  * phase such that the largest-modulus component is real positive],
- * resid[n_eig]; sorted by |lambda| ascending, then lambda.  n_eig <= n_tv.
+ * resid[n_eig]; sorted by |lambda| ascending, then lambda.  Iterated vectors
+ * beyond the n_tv test vectors start from Philox uniforms (stream 0x5EED0003,
+ * the setup's seed) smoothed by setup_smooth two-grid iterations; P always holds
+ * the first n_tv of them.  n_eig + n_guard <= 64.
  * ENOCONV when max_sweeps is hit (outputs hold the current iterates). */
 int mgeig_eigensolve(mgeig_ctx *ctx, int n_eig, double tol, double *evals, double *evecs,
                      double *resid, mgeig_stats *stats);

@@ -288,6 +288,8 @@ class TwoGrid:
         self.set_test_vectors(W)
         self.sap = SAP(op, self.p["sap_block"]) if self.p["smoother"] == "sap" else None
 
+    deflate_active = True     # the setup switches deflation off (its test vectors are no eigenvectors yet)
+
     def set_test_vectors(self, W: np.ndarray):
         self.W = np.array(W)
         self.P = Interpolation(self.W, self.p["agg"])
@@ -307,7 +309,7 @@ class TwoGrid:
     def coarse_solve(self, rc: np.ndarray, sigma: float) -> np.ndarray:
         C = self.coarse
         gm = dict(tol=self.p["coarse_tol"], restart=self.p["coarse_restart"], maxiter=self.p["coarse_maxiter"])
-        if not self.p.get("coarse_deflate", True):
+        if not (self.p.get("coarse_deflate", True) and self.deflate_active):
             ec, _ = krylov.gmres(lambda v: C.apply_dsigma(v, sigma), C.gamma5(rc), **gm)
             return ec
         Wc, AW, Einv = self.deflation(sigma)
@@ -354,11 +356,11 @@ DEFAULT_PARAMS = dict(
     gmres_smooth_k=8,
     coarse_tol=5e-2,
     coarse_restart=30,
-    coarse_maxiter=300,
+    coarse_maxiter=200,
     coarse_deflate=True,
     ritz_each_sweep=True,
     outer_restart=20,
-    outer_maxiter=200,
+    outer_maxiter=50,
     solve_tol=1e-2,
     setup_smooth=3,
     setup_iters=10,

@@ -3,17 +3,20 @@
 Setup (Sec. 2.1, the paragraph after Algorithm 1): a few smoother iterations
 on random vectors give the first test vectors and P; then, a few times, one
 multigrid iteration is applied to every test vector, the test vectors are
-orthonormalised again and P and the coarse operator are rebuilt.  The smoother
+orthonormalised again and P and the coarse operator are rebuilt (the setup's
+coarse solves run without deflation: its test vectors are no eigenvector
+approximations yet).  The smoother
 iterations on a random w approximate Q^-1 w (SAP: D x = gamma5 w from x = 0);
 one multigrid iteration on w is w <- B w with B the two-grid preconditioner at
 sigma = 0.
 
 Before the iteration the test vectors are rotated to the Ritz vectors of Q in
-their span and ordered by |theta| (same span, hence the same P); the first
-N_eig + N_guard are the start vectors v_i of Algorithm 1, and the N_eig pairs of
-smallest |lambda| are returned.  The guard vectors (N_guard = min(N_tv - N_eig,
-N_eig) by default) lower the chance of missing a wanted pair, the failure the
-paper describes after Algorithm 1.
+their span and ordered by |theta| (same span, hence the same P); N_eig + N_guard
+start vectors v_i of Algorithm 1 follow (beyond N_tv: extra_start_vectors), and
+the N_eig pairs of smallest |lambda| are returned.  The guard vectors
+(N_guard = max(N_eig, N_tv) by default) lower the chance of missing a wanted
+pair, the failure the paper describes after Algorithm 1, by spanning whole
+clusters of nearly equal eigenvalues.
 
 Algorithm 1, per sweep over the unconverged i:
     sigma   = lambda_i * max(1 - eps_i, 0)                 (damped shift)
@@ -22,8 +25,10 @@ Algorithm 1, per sweep over the unconverged i:
     v_i    <- v_i / ||v_i||
     update v_i in P (rebuild P and the coarse operator)
     lambda_i = <v_i|Q|v_i>,  eps_i = ||Q v_i - lambda_i v_i||
-starting from lambda_i = 0, eps_i = 1.  P is built from [v_1..v_N_eig] followed by
-the remaining test vectors when N_tv > N_eig.
+starting from lambda_i = 0, eps_i = 1.  P is built from the first N_tv of
+[v_1, v_2, ...] followed by the remaining test vectors when fewer vectors are
+iterated than there are test vectors; updating a v_i beyond the first N_tv leaves P
+unchanged.
 
 After every sweep (with ritz_each_sweep) the iterated vectors are replaced by the
 Ritz vectors of Q in their span, ordered by |theta| (lambda_i = theta_i,
@@ -64,9 +69,11 @@ def setup(op: dirac.WilsonClover, W0: np.ndarray, params: dict):
             W.append(x)
     W = orthonormalise(np.array(W))
     B = mg.TwoGrid(op, W, p)
+    B.deflate_active = False
     for _ in range(p["setup_iters"]):
         W = orthonormalise(np.array([B(w, 0.0) for w in W]))
         B.set_test_vectors(W)
+    B.deflate_active = True
     return W, B
 
 
@@ -89,21 +96,31 @@ def rayleigh(op: dirac.WilsonClover, v: np.ndarray):
 
 
 def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
-        n_eig: int, eps: float, params: dict, max_sweeps: int = 50, log=None):
-    """Algorithm 1.  Returns (lambda, vectors, eps_i, stats), sorted by |lambda|."""
+        n_eig: int, eps: float, params: dict, max_sweeps: int = 50, log=None, n_want: int = None):
+    """Algorithm 1.  Returns (lambda, vectors, eps_i, stats), sorted by |lambda|.
+
+    With ritz_each_sweep the vectors stay in Ritz order and the iteration stops
+    once the n_want lowest pairs are converged (the others only widen the span);
+    otherwise all n_eig must converge."""
     p = params
     ritz_each_sweep = p.get("ritz_each_sweep", True)
+    n_want = n_eig if n_want is None else n_want
     V = [v.copy() for v in V[:n_eig]]
     lam = np.zeros(n_eig)
     res = np.ones(n_eig)
     stats = dict(sweeps=0, solves=0, outer_iters=0)
 
+    ntv = B.P.ntv
+
     def rebuild():
-        W = np.array(V + ([] if extra is None else list(extra)))
+        W = np.array(V + ([] if extra is None else list(extra)))[:ntv]
         B.set_test_vectors(W)
 
+    def unconverged():
+        return np.any(res[:n_want] > eps) if ritz_each_sweep else np.any(res > eps)
+
     rebuild()
-    while np.any(res > eps) and stats["sweeps"] < max_sweeps:
+    while unconverged() and stats["sweeps"] < max_sweeps:
         stats["sweeps"] += 1
         for i in range(n_eig):
             if res[i] <= eps:
@@ -118,7 +135,8 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
                 for j in range(i):
                     x = x - coeff[j] * V[j]
             V[i] = x / dirac.norm(x)
-            rebuild()
+            if i < ntv:
+                rebuild()
             lam[i], res[i] = rayleigh(op, V[i])
             if log is not None:
                 log(f"sweep {stats['sweeps']} i={i} sigma={sigma:.6e} lambda={lam[i]:.12e} eps={res[i]:.3e} "
@@ -133,14 +151,32 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
     return lam[order], np.array(V)[order], res[order], stats
 
 
+def extra_start_vectors(op: dirac.WilsonClover, B: mg.TwoGrid, W: np.ndarray, n: int, seed: int, params: dict):
+    """n further start vectors for Algorithm 1 beyond the N_tv test vectors:
+    Philox uniforms (tag TAG_EXTRA), setup_smooth two-grid iterations at sigma = 0
+    with the setup's P, orthonormalised against W and each other."""
+    import synth
+    X = synth.uniform_vectors(op.dims, n, seed, tag=synth.TAG_EXTRA)
+    B.deflate_active = False
+    for _ in range(params["setup_smooth"]):
+        X = np.array([B(x, 0.0) for x in X])
+    B.deflate_active = True
+    return orthonormalise(np.concatenate([W, X]))[len(W):]
+
+
 def eigensolve(op: dirac.WilsonClover, W0: np.ndarray, n_eig: int, eps: float, params: dict,
-               max_sweeps: int = 50, log=None, n_guard: int = -1):
-    """Setup, Ritz rotation of the test vectors, then Algorithm 1 on n_eig + n_guard vectors."""
+               max_sweeps: int = 50, log=None, n_guard: int = -1, seed: int = 0):
+    """Setup, Ritz rotation of the test vectors, then Algorithm 1 on n_eig + n_guard
+    vectors.  Vectors beyond the N_tv test vectors come from extra_start_vectors;
+    P is always built from the N_tv iterated vectors of smallest |theta| (in the
+    Ritz order) plus, when N_tv exceeds the number iterated, the remaining test vectors."""
     W, B = setup(op, W0, params)
-    W, _ = ritz_rotate(op, W)
-    spare = W.shape[0] - n_eig
-    guard = min(spare, n_eig) if n_guard < 0 else min(spare, n_guard)
+    ntv = W.shape[0]
+    guard = max(n_eig, ntv) if n_guard < 0 else n_guard
     n_run = n_eig + guard
+    if n_run > ntv:
+        W = np.concatenate([W, extra_start_vectors(op, B, W, n_run - ntv, seed, params)])
+    W, _ = ritz_rotate(op, W)
     extra = W[n_run:] if W.shape[0] > n_run else None
-    lam, V, res, st = rqi(op, W[:n_run], extra, B, n_run, eps, params, max_sweeps, log)
+    lam, V, res, st = rqi(op, W[:n_run], extra, B, n_run, eps, params, max_sweeps, log, n_want=n_eig)
     return lam[:n_eig], V[:n_eig], res[:n_eig], st

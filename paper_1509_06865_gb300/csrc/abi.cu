@@ -90,9 +90,9 @@ void mgeig_default_params(mgeig_params *p) {
     p->setup_smooth = 3;
     p->setup_iters = 10;
     p->outer_restart = 20;
-    p->outer_maxiter = 200;
+    p->outer_maxiter = 50;
     p->coarse_restart = 30;
-    p->coarse_maxiter = 300;
+    p->coarse_maxiter = 200;
     p->coarse_tol = 5e-2;
     p->solve_tol = 1e-2;
     p->precision = MGEIG_MIXED;
@@ -492,7 +492,7 @@ int mgeig_eigensolve(mgeig_ctx *ctx, int n_eig, double tol, double *evals, doubl
                      mgeig_stats *stats) {
     return guarded(ctx, [&](Ctx &c) {
         if (!c.have_setup) return MGEIG_ENOTSETUP;
-        if (n_eig < 1 || n_eig > c.prm.n_tv || !(tol > 0)) return MGEIG_EINVAL;
+        if (n_eig < 1 || n_eig > MAX_ITERATED || !(tol > 0)) return MGEIG_EINVAL;
         auto t0 = std::chrono::steady_clock::now();
         begin_stats(c);
         int rc = eigensolve(c, n_eig, tol, evals, evecs, resid);

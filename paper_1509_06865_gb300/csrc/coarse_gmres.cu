@@ -154,20 +154,11 @@ __device__ __forceinline__ cpx<R> g5c(const CGArgs<R> &a, int t, cpx<R> v) {
     return (t % (2 * a.ntv)) >= a.ntv ? -v : v;
 }
 
-// warp-reduce (re, im) and park it in sh[warp][i]
-__device__ __forceinline__ void warp_park(double re, double im, int i, double2 *sh) {
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-    }
-    if ((threadIdx.x & 31) == 0) sh[(threadIdx.x >> 5) * WS + i] = make_double2(re, im);
-}
-
 template <typename R>
 __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a) {
-    __shared__ double2 wsum[(CG_THREADS / 32) * WS];
-    __shared__ double2 h[WS];
-    __shared__ double2 Rm[(CG_MAXM + 1) * CG_MAXM];   // rotated Hessenberg, column-major
+    __shared__ double2 wpart[WS];                    // this block's partial sums
+    __shared__ double2 h[WS];                        // grid-wide sums after a gather
+    __shared__ double2 Rm[(CG_MAXM + 1) * CG_MAXM];  // rotated Hessenberg, column-major
     __shared__ double cs[CG_MAXM];
     __shared__ double2 sn[CG_MAXM], g[CG_MAXM + 1], y[CG_MAXM];
     __shared__ double scale[CG_MAXM + 1];
@@ -176,6 +167,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     __shared__ int stop;
     const unsigned int G = gridDim.x;
     const int nw = CG_THREADS / 32;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int rows_per_block = (a.n + G - 1) / G;
     const int r0 = blockIdx.x * rows_per_block;
     const int r1 = min(a.n, r0 + rows_per_block);
@@ -186,21 +178,30 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     if (threadIdx.x < CG_MAXK) { tc[threadIdx.x] = make_double2(0, 0); t0[threadIdx.x] = make_double2(0, 0); }
     __syncthreads();
 
-    // block partials in wsum[.][0..cnt) -> mypart[off..off+cnt)
-    auto flush = [&](int off, int cnt) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    // wpart[i] = sc_i <X_i, u> over the owned rows, i < cnt: warp i takes value i,
+    // its lanes stride over the rows (u complete on the owned rows)
+    auto dots = [&](int cnt, auto vec, auto sc, const cpx<R> *u) {
+        for (int i = wp; i < cnt; i += nw) {
+            const cpx<R> *xi = vec(i);
             double sr = 0, si = 0;
-            for (int w = 0; w < nw; ++w) { double2 p = wsum[w * WS + i]; sr += p.x; si += p.y; }
-            mypart[off + i] = make_double2(sr, si);
+            for (int t = r0 + lane; t < r1; t += 32) {
+                cpx<R> p = xi[t], q = u[t];
+                sr += (double)p.re * q.re + (double)p.im * q.im;
+                si += (double)p.re * q.im - (double)p.im * q.re;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) wpart[i] = make_double2(sr * sc(i), si * sc(i));
         }
     };
-    // after a barrier: h[i] = sum over blocks of partial[.][off + i]; warp i
-    // reads the G partials of value i (lanes stride over the blocks) and
-    // reduces them in a fixed order
-    auto gather = [&](int off, int cnt) {
-        const int lane = threadIdx.x & 31;
-        for (int i = threadIdx.x >> 5; i < cnt; i += nw) {
+    // publish wpart[0..cnt) to this block's partial slots, barrier, h = grid sums
+    auto reduce = [&](int off, int cnt) -> bool {
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) mypart[off + i] = wpart[i];
+        if (!grid_sync(a.st, G, a.timeout)) return false;
+        for (int i = wp; i < cnt; i += nw) {
             double sr = 0, si = 0;
             for (unsigned int q = lane; q < G; q += 32) {
                 double2 p = __ldcg(a.partial + (size_t)q * CG_SLOTS + off + i);
@@ -213,22 +214,40 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             if (lane == 0) h[i] = make_double2(sr, si);
         }
         __syncthreads();
+        return true;
     };
-    // tc = E^-1 W^dag u (grid-wide); u complete on the owned rows
-    auto deflation_coeffs = [&](const cpx<R> *u) -> bool {
-        for (int i = 0; i < k; ++i) {
-            const cpx<R> *wi = a.W + (size_t)i * a.n;
-            double sr = 0, si = 0;
-            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-                cpx<R> p = wi[t], q = u[t];
-                sr += (double)p.re * q.re + (double)p.im * q.im;
-                si += (double)p.re * q.im - (double)p.im * q.re;
+    // u[t] = f(t, u[t], sum_i coef_i X_i[t]) on the owned rows; TPR lanes share a row
+    auto combine = [&](int cnt, auto vec, auto coef, cpx<R> *u, auto f) {
+        const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
+        for (int tb = r0; tb < r1; tb += ngrp) {
+            const int t = tb + grp;
+            cpx<R> acc0, acc1;
+            if (t < r1) {
+                int i = q;
+                for (; i + TPR < cnt; i += 2 * TPR) {
+                    cmac(acc0, coef(i), vec(i)[t]);
+                    cmac(acc1, coef(i + TPR), vec(i + TPR)[t]);
+                }
+                if (i < cnt) cmac(acc0, coef(i), vec(i)[t]);
             }
-            warp_park(sr, si, i, wsum);
+            cpx<R> acc = acc0 + acc1;
+            for (int o = 1; o < TPR; o <<= 1) {
+                acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+                acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+            }
+            if (t < r1 && q == 0) u[t] = f(t, u[t], acc);
         }
-        flush(OFF_P, k);
-        if (!grid_sync(a.st, G, a.timeout)) return false;
-        gather(OFF_P, k);
+        __syncthreads();
+    };
+    auto one = [](int) { return 1.0; };
+    auto Wvec = [&](int i) { return a.W + (size_t)i * a.n; };
+    auto AWvec = [&](int i) { return a.AW + (size_t)i * a.n; };
+    auto Vvec = [&](int i) { return a.V + (size_t)i * a.n; };
+
+    // tc = E^-1 W^dag u
+    auto deflation_coeffs = [&](const cpx<R> *u) -> bool {
+        dots(k, Wvec, one, u);
+        if (!reduce(OFF_P, k)) return false;
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
             double sr = 0, si = 0;
             for (int l = 0; l < k; ++l) {
@@ -241,17 +260,10 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         __syncthreads();
         return true;
     };
-    // u <- gamma5^c (u - A W tc) on the owned rows
+    // u <- gamma5^c (u - A W tc)
     auto project_g5 = [&](cpx<R> *u) {
-        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-            cpx<R> q = u[t];
-            for (int i = 0; i < k; ++i) {
-                const cpx<R> ti((R)tc[i].x, (R)tc[i].y);
-                q = q - ti * a.AW[(size_t)i * a.n + t];
-            }
-            u[t] = g5c(a, t, q);
-        }
-        __syncthreads();
+        combine(k, AWvec, [&](int i) { return cpx<R>((R)tc[i].x, (R)tc[i].y); }, u,
+                [&](int t, cpx<R> ut, cpx<R> s) { return g5c(a, t, ut - s); });
     };
     // u = gamma5^c Pi (Q_c - sigma)(s v) on the owned rows
     auto apply_op = [&](const cpx<R> *v, R s, cpx<R> *u) -> bool {
@@ -268,16 +280,21 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             cpx<R> q = v[t];
             acc += (double)q.re * q.re + (double)q.im * q.im;
         }
-        warp_park(acc, 0.0, 0, wsum);
-        flush(OFF_N, 1);
-        if (!grid_sync(a.st, G, a.timeout)) return false;
-        gather(OFF_N, 1);
-        return true;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        __shared__ double nsum[CG_THREADS / 32];
+        if (lane == 0) nsum[wp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s2 = 0;
+            for (int w = 0; w < nw; ++w) s2 += nsum[w];
+            wpart[0] = make_double2(s2, 0);
+        }
+        return reduce(OFF_N, 1);
     };
 
     // rhs = gamma5^c Pi r_c, t0 = E^-1 W^dag r_c, x = 0.  The tolerance refers
     // to ||r_c||: when r_c lies mostly in span(W) the projected right-hand side
-    // is tiny and needs no further reduction.
+    // is small and needs no further reduction.
     for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) { a.rhs[t] = a.b[t]; a.x[t] = cpx<R>(); }
     __syncthreads();
     if (!grid_norm2(a.rhs)) return;
@@ -318,38 +335,19 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         int kk = 0;
         bool conv = false;
         for (int j = 0; j < mm; ++j) {
-            cpx<R> *vj = a.V + (size_t)j * a.n;
             cpx<R> *w = a.V + (size_t)(j + 1) * a.n;
-            if (!apply_op(vj, (R)scale[j], w)) return;
+            if (!apply_op(Vvec(j), (R)scale[j], w)) return;
             for (int pass = 0; pass < 2; ++pass) {
-                for (int i = 0; i <= j; ++i) {
-                    const cpx<R> *vi = a.V + (size_t)i * a.n;
-                    double sr = 0, si = 0;
-                    for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-                        cpx<R> p = vi[t], q = w[t];
-                        sr += (double)p.re * q.re + (double)p.im * q.im;
-                        si += (double)p.re * q.im - (double)p.im * q.re;
-                    }
-                    warp_park(sr * scale[i], si * scale[i], i, wsum);
-                }
-                flush(pass == 0 ? OFF_H1 : OFF_H2, j + 1);
-                if (!grid_sync(a.st, G, a.timeout)) return;
-                gather(pass == 0 ? OFF_H1 : OFF_H2, j + 1);
+                dots(j + 1, Vvec, [&](int i) { return scale[i]; }, w);
+                if (!reduce(pass == 0 ? OFF_H1 : OFF_H2, j + 1)) return;
                 if (threadIdx.x == 0) {
                     for (int i = 0; i <= j; ++i) {
                         double2 &col = Rm[j * (CG_MAXM + 1) + i];
                         col = pass == 0 ? h[i] : make_double2(col.x + h[i].x, col.y + h[i].y);
                     }
                 }
-                for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-                    cpx<R> q = w[t];
-                    for (int i = 0; i <= j; ++i) {
-                        const cpx<R> hi((R)(h[i].x * scale[i]), (R)(h[i].y * scale[i]));
-                        q = q - hi * a.V[(size_t)i * a.n + t];
-                    }
-                    w[t] = q;
-                }
-                __syncthreads();
+                combine(j + 1, Vvec, [&](int i) { return cpx<R>((R)(h[i].x * scale[i]), (R)(h[i].y * scale[i])); }, w,
+                        [](int, cpx<R> ut, cpx<R> s) { return ut - s; });
             }
             if (!grid_norm2(w)) return;
             if (threadIdx.x == 0) {
@@ -404,14 +402,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             }
         }
         __syncthreads();
-        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-            cpx<R> q = a.x[t];
-            for (int i = 0; i < kk; ++i) {
-                const cpx<R> yi((R)(y[i].x * scale[i]), (R)(y[i].y * scale[i]));
-                q = q + yi * a.V[(size_t)i * a.n + t];
-            }
-            a.x[t] = q;
-        }
+        combine(kk, Vvec, [&](int i) { return cpx<R>((R)(y[i].x * scale[i]), (R)(y[i].y * scale[i])); }, a.x,
+                [](int, cpx<R> ut, cpx<R> s) { return ut + s; });
         have_x = true;
         its += kk;
         if (!grid_sync(a.st, G, a.timeout)) return;   // x complete before any matvec on it
@@ -425,14 +417,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         qmatvec<R>(a, a.x, R(1), u, r0, r1);
         __syncthreads();
         if (!deflation_coeffs(u)) return;
-        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-            cpx<R> q = a.x[t];
-            for (int i = 0; i < k; ++i) {
-                const cpx<R> ci((R)(t0[i].x - tc[i].x), (R)(t0[i].y - tc[i].y));
-                q = q + ci * a.W[(size_t)i * a.n + t];
-            }
-            a.x[t] = q;
-        }
+        combine(k, Wvec, [&](int i) { return cpx<R>((R)(t0[i].x - tc[i].x), (R)(t0[i].y - tc[i].y)); }, a.x,
+                [](int, cpx<R> ut, cpx<R> s) { return ut + s; });
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.st->iters, its);
 }

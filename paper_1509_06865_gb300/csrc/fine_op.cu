@@ -430,13 +430,13 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
     }
 }
 
-__global__ void random_spinor_kernel(int V, int n, uint32_t k0, uint32_t k1, double2 *__restrict__ out) {
+__global__ void random_spinor_kernel(int V, int n, uint32_t k0, uint32_t k1, uint32_t tag, double2 *__restrict__ out) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)V * n * 6) return;
     const int q = (int)(i % 6);
     const int s = (int)((i / 6) % V);
     const int j = (int)(i / ((size_t)6 * V));
-    uint32_t ctr[4] = {(uint32_t)s, (uint32_t)q, (uint32_t)j, 0x5EED0001u};
+    uint32_t ctr[4] = {(uint32_t)s, (uint32_t)q, (uint32_t)j, tag};
     philox4x32_10(ctr, k0, k1);
     const double sc = 1.0 / 2147483648.0;
     double2 *o = out + (size_t)j * 12 * V;
@@ -444,10 +444,10 @@ __global__ void random_spinor_kernel(int V, int n, uint32_t k0, uint32_t k1, dou
     o[(size_t)(2 * q + 1) * V + s] = make_double2((double)(int32_t)ctr[2] * sc, (double)(int32_t)ctr[3] * sc);
 }
 
-void random_spinors(Ctx &c, uint64_t seed, void *out64, int n) {
+void random_spinors(Ctx &c, uint64_t seed, void *out64, int n, uint32_t tag) {
     size_t tot = (size_t)c.g.V * n * 6;
     random_spinor_kernel<<<grid_for(tot, 256), 256, 0, c.stream>>>(c.g.V, n, (uint32_t)(seed & 0xFFFFFFFFu),
-                                                                   (uint32_t)(seed >> 32), static_cast<double2 *>(out64));
+                                                                   (uint32_t)(seed >> 32), tag, static_cast<double2 *>(out64));
     MG_CHECK_LAUNCH();
 }
 

@@ -101,7 +101,8 @@ void pack_spinor_f64(Ctx &c, const double *host_layout_dev, void *out, int n);
 void unpack_spinor_f64(Ctx &c, const void *in, double *host_layout_dev, int n);
 void convert_f64_to_f32(Ctx &c, const void *in64, void *out32, size_t ncomplex);
 void convert_f32_to_f64(Ctx &c, const void *in32, void *out64, size_t ncomplex);
-void random_spinors(Ctx &c, uint64_t seed, void *out64, int n);
+void random_spinors(Ctx &c, uint64_t seed, void *out64, int n, uint32_t tag);
+constexpr int MAX_ITERATED = 64;   // vectors iterated by Algorithm 1
 
 // ----- BLAS-1 on flat complex arrays (blas.cu) -----
 // Results of reductions land in device memory (cpx<double>); *_host variants sync.
@@ -146,6 +147,8 @@ struct Ctx {
     mgeig_params prm;
     bool have_gauge = false;
     bool have_setup = false;
+    bool in_setup = false;    // the setup's coarse solves run without deflation
+    uint64_t setup_seed = 0;
     Timer timer;
 
     // fine fields

@@ -159,6 +159,8 @@ struct Ctx::Work {
     DevBuf rc, ec, ct;           // coarse vectors
     DevBuf cgV, cgRhs, cgP;      // persistent coarse solver: basis, rhs, partial sums
     DevBuf Wc, AWc, Edev, Einv;  // deflation: P^dag w_j, (Q_c - sigma) P^dag w_j, E, E^-1
+    DevBuf Mextra, Xall;         // Algorithm 1 vectors beyond the N_tv test vectors; rotation scratch
+    std::vector<void *> modes;   // iterated vectors: W[0..N_tv) then the extra ones
     bool defl_valid = false;
     double defl_sigma = 0;
     std::vector<void *> W, P64, P;
@@ -216,6 +218,7 @@ void mg_free(Ctx &c) {
     w.rc.free(); w.ec.free(); w.ct.free();
     w.cgV.free(); w.cgRhs.free(); w.cgP.free();
     w.Wc.free(); w.AWc.free(); w.Edev.free(); w.Einv.free();
+    w.Mextra.free(); w.Xall.free();
     delete c.work;
     c.work = nullptr;
     c.Dc.free();
@@ -392,7 +395,7 @@ static bool invert(int n, std::vector<cpx<double>> A, std::vector<cpx<double>> &
 template <typename R>
 static void deflation_prepare(Ctx &c, double sigma) {
     Ctx::Work &w = *c.work;
-    if (!c.prm.coarse_deflate || (w.defl_valid && w.defl_sigma == sigma)) return;
+    if (!c.prm.coarse_deflate || c.in_setup || (w.defl_valid && w.defl_sigma == sigma)) return;
     const int k = c.prm.n_tv;
     const size_t n = c.coarse_ncpx(), vb = cR_bytes(c);
     std::vector<const void *> Wp(k);
@@ -425,7 +428,7 @@ static void coarse_solve(Ctx &c, double sigma, const void *rc, void *ec) {
     B.rhs = &w.cgRhs;
     B.partial = &w.cgP;
     B.state = dslot(c, CGS);
-    B.k = c.prm.coarse_deflate ? c.prm.n_tv : 0;
+    B.k = (c.prm.coarse_deflate && !c.in_setup) ? c.prm.n_tv : 0;
     B.W = w.Wc.p;
     B.AW = w.AWc.p;
     B.Einv = w.Einv.p;
@@ -558,7 +561,8 @@ template <typename R>
 static void setup_impl(Ctx &c, uint64_t seed) {
     Ctx::Work &w = *c.work;
     const int ntv = c.prm.n_tv;
-    random_spinors(c, seed, w.Wall.p, ntv);
+    random_spinors(c, seed, w.Wall.p, ntv, 0x5EED0001u);
+    c.setup_seed = seed;
     for (int j = 0; j < ntv; ++j) smooth_random<R>(c, w.W[j]);
     orthonormalise(c, w.W, ntv);
     mg_rebuild(c);
@@ -580,8 +584,15 @@ static void setup_impl(Ctx &c, uint64_t seed) {
 }
 
 void setup(Ctx &c, uint64_t seed) {
-    if (c.mixed()) setup_impl<float>(c, seed);
-    else setup_impl<double>(c, seed);
+    c.in_setup = true;
+    try {
+        if (c.mixed()) setup_impl<float>(c, seed);
+        else setup_impl<double>(c, seed);
+    } catch (...) {
+        c.in_setup = false;
+        throw;
+    }
+    c.in_setup = false;
     c.have_setup = true;
 }
 
@@ -700,15 +711,16 @@ static void herm_eig(int n, std::vector<cpx<double>> A, std::vector<double> &w, 
     for (int i = 0; i < n; ++i) w[i] = a(i, i).re;
 }
 
-// Ritz vectors of Q in span(W[0..n)), ordered by |theta| then theta, written
-// back into W[0..n).  Scratch: the P64 and RR vector sets (P is rebuilt after).
-static void ritz_rotate(Ctx &c, int n) {
+// Ritz vectors of Q in span(X[0..n)), ordered by |theta| then theta, written
+// back into X[0..n).  Scratch: the Xall vector set.
+static void ritz_rotate(Ctx &c, std::vector<void *> &Xv, int n) {
     Ctx::Work &w = *c.work;
     const size_t N = c.fine_ncpx();
+    w.Xall.alloc(f64_bytes(c) * n);
     std::vector<cpx<double>> H((size_t)n * n);
-    std::vector<const void *> X(w.W.begin(), w.W.begin() + n);
+    std::vector<const void *> X(Xv.begin(), Xv.begin() + n);
     for (int j = 0; j < n; ++j) {
-        apply_fine<double>(c, MODE_QSIGMA, 0.0, w.W[j], w.q64.p);
+        apply_fine<double>(c, MODE_QSIGMA, 0.0, Xv[j], w.q64.p);
         blas_multidot<double>(c, X.data(), n, w.q64.p, N, dslot(c, H1));
         fetch(c, n);
         for (int i = 0; i < n; ++i) H[(size_t)i * n + j] = *hslot(c, H1 + i);
@@ -731,10 +743,11 @@ static void ritz_rotate(Ctx &c, int n) {
     for (int k = 0; k < n; ++k) {
         std::vector<cpx<double>> coef(n);
         for (int i = 0; i < n; ++i) coef[i] = Y[(size_t)i * n + ord[k]];
-        blas_zero<double>(c, w.P64[k], N);
-        blas_multi_axpy<double>(c, w.P64[k], X.data(), n, upload(c, coef), 1.0, N);
+        void *dst = static_cast<char *>(w.Xall.p) + f64_bytes(c) * k;
+        blas_zero<double>(c, dst, N);
+        blas_multi_axpy<double>(c, dst, X.data(), n, upload(c, coef), 1.0, N);
     }
-    for (int k = 0; k < n; ++k) blas_copy<double>(c, w.P64[k], w.W[k], N);
+    for (int k = 0; k < n; ++k) blas_copy<double>(c, static_cast<char *>(w.Xall.p) + f64_bytes(c) * k, Xv[k], N);
 }
 
 // lambda = <v|Q v>, eps^2 = ||Q v - lambda v||^2 ; returns (lambda, eps)
@@ -752,18 +765,48 @@ static std::pair<double, double> rayleigh(Ctx &c, const void *v) {
     return {lam, eps};
 }
 
+// Start vectors of Algorithm 1 beyond the N_tv test vectors: Philox uniforms
+// (stream 0x5EED0003), setup_smooth two-grid iterations at sigma = 0 with the
+// setup's P, then Gram-Schmidt against all earlier vectors.
+template <typename R>
+static void extra_start_vectors(Ctx &c, int n_tv, int n_run) {
+    Ctx::Work &w = *c.work;
+    const int n_extra = n_run - n_tv;
+    random_spinors(c, c.setup_seed, w.Mextra.p, n_extra, 0x5EED0003u);
+    c.in_setup = true;
+    for (int k = 0; k < c.prm.setup_smooth; ++k)
+        for (int j = n_tv; j < n_run; ++j) {
+            mg_cycle_f64<R>(c, 0.0, w.modes[j], w.t64.p);
+            blas_copy<double>(c, w.t64.p, w.modes[j], c.fine_ncpx());
+        }
+    c.in_setup = false;
+    orthonormalise(c, w.modes, n_run);
+}
+
 int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host, double *resid) {
     Ctx::Work &w = *c.work;
     const size_t N = c.fine_ncpx();
-    const int spare = c.prm.n_tv - n_want;
-    const int guard = c.prm.n_guard < 0 ? std::min(spare, n_want) : std::min(spare, c.prm.n_guard);
+    const int ntv = c.prm.n_tv;
+    const int guard = c.prm.n_guard < 0 ? std::min(std::max(n_want, ntv), MAX_ITERATED - n_want) : c.prm.n_guard;
     const int n_eig = n_want + guard;
-    ritz_rotate(c, c.prm.n_tv);
+    MG_REQUIRE(n_eig <= MAX_ITERATED, MGEIG_EINVAL);
+    w.modes.assign(w.W.begin(), w.W.end());
+    if (n_eig > ntv) {
+        w.Mextra.alloc(f64_bytes(c) * (n_eig - ntv));
+        for (int j = ntv; j < n_eig; ++j) w.modes.push_back(static_cast<char *>(w.Mextra.p) + f64_bytes(c) * (j - ntv));
+        if (c.mixed()) extra_start_vectors<float>(c, ntv, n_eig);
+        else extra_start_vectors<double>(c, ntv, n_eig);
+    }
+    std::vector<void *> &M = w.modes;
+    ritz_rotate(c, M, std::max(ntv, n_eig));
     mg_rebuild(c);
     std::vector<double> lam(n_eig, 0.0), eps(n_eig, 1.0);
     int sweeps = 0;
+    // with the per-sweep Rayleigh-Ritz step the vectors stay in Ritz order and
+    // only the n_want lowest must converge (the others widen the span)
     auto unconverged = [&]() {
-        for (int i = 0; i < n_eig; ++i)
+        const int n = c.prm.ritz_each_sweep ? n_want : n_eig;
+        for (int i = 0; i < n; ++i)
             if (eps[i] > tol) return true;
         return false;
     };
@@ -775,10 +818,10 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             const double sigma = lam[i] * std::max(1.0 - eps[i], 0.0);
             const double t0 = now_s();
             const int outer0 = c.st.outer_iters;
-            int rc = fgmres_solve(c, sigma, w.W[i], w.x64.p, c.prm.solve_tol);
+            int rc = fgmres_solve(c, sigma, M[i], w.x64.p, c.prm.solve_tol);
             if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
             if (i > 0) {
-                std::vector<const void *> X(w.W.begin(), w.W.begin() + i);
+                std::vector<const void *> X(M.begin(), M.begin() + i);
                 for (int pass = 0; pass < 2; ++pass) {
                     blas_multidot<double>(c, X.data(), i, w.x64.p, N, dslot(c, H1));
                     blas_multi_axpy<double>(c, w.x64.p, X.data(), i, dslot(c, H1), -1.0, N);
@@ -789,9 +832,9 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             const double nrm = std::sqrt(hslot(c, HN)->re);
             MG_REQUIRE(std::isfinite(nrm) && nrm > 0, MGEIG_EBREAKDOWN);
             blas_scale<double>(c, cpx<double>(1.0 / nrm), w.x64.p, N);
-            blas_copy<double>(c, w.x64.p, w.W[i], N);
-            mg_rebuild(c);
-            auto le = rayleigh(c, w.W[i]);
+            blas_copy<double>(c, w.x64.p, M[i], N);
+            if (i < ntv) mg_rebuild(c);   // P holds the first N_tv iterated vectors
+            auto le = rayleigh(c, M[i]);
             lam[i] = le.first;
             eps[i] = le.second;
             if (log_on()) {
@@ -804,9 +847,9 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
         }
         if (c.prm.ritz_each_sweep) {
             // Rayleigh-Ritz on the iterated vectors: separates nearly equal eigenvalues
-            ritz_rotate(c, n_eig);
+            ritz_rotate(c, M, n_eig);
             for (int i = 0; i < n_eig; ++i) {
-                auto le = rayleigh(c, w.W[i]);
+                auto le = rayleigh(c, M[i]);
                 lam[i] = le.first;
                 eps[i] = le.second;
             }
@@ -834,7 +877,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
     if (evecs_host) {
         // host layout, unit norm, largest-modulus component real positive
         for (int k = 0; k < n_want; ++k) {
-            unpack_spinor_f64(c, w.W[ord[k]], static_cast<double *>(c.staging.p), 1);
+            unpack_spinor_f64(c, M[ord[k]], static_cast<double *>(c.staging.p), 1);
             MG_CUDA(cudaMemcpyAsync(evecs_host + (size_t)k * N * 2, c.staging.p, N * 16, cudaMemcpyDeviceToHost, c.stream));
             sync(c);
             double *v = evecs_host + (size_t)k * N * 2;

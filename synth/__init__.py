@@ -36,6 +36,7 @@ _MASK32 = np.uint64(0xFFFFFFFF)
 TAG_GAUGE = 0x6A09E667
 TAG_TESTVEC = 0x5EED0001
 TAG_RHS = 0x5EED0002
+TAG_EXTRA = 0x5EED0003
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
