@@ -103,6 +103,10 @@ typedef struct mgeig_params {
                              deflation), 0: plain                               */
     int ritz_each_sweep;  /* 1: after every sweep of Algorithm 1 the iterated
                              vectors become the Ritz vectors of Q in their span */
+    double shift_floor;   /* damping floor: sigma = lambda max(1 - max(eps,
+                             shift_floor), 0); keeps the shifted system solvable
+                             by the single-precision preconditioner              */
+    int guard_maxiter;    /* FGMRES step cap for the guard vectors' solves     */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */
@@ -242,6 +246,11 @@ int mgeig_eigensolve(mgeig_ctx *ctx, int n_eig, double tol, double *evals, doubl
 int mgeig_set_timing(mgeig_ctx *ctx, int on);
 int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms,
                        double *bytes, const char **names);
+
+/* The cudaStream_t (as void *) on which every call of this context launches
+ * its kernels, for callers that record CUDA events around device-pointer calls
+ * such as mgeig_apply_dev.  Owned by the context. */
+int mgeig_get_stream(mgeig_ctx *ctx, void **stream);
 
 /* Name of a status code. */
 const char *mgeig_strerror(int status);

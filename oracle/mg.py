@@ -359,6 +359,8 @@ DEFAULT_PARAMS = dict(
     coarse_maxiter=200,
     coarse_deflate=True,
     ritz_each_sweep=True,
+    shift_floor=1e-5,
+    guard_maxiter=8,
     outer_restart=20,
     outer_maxiter=50,
     solve_tol=1e-2,

@@ -19,7 +19,8 @@ pair, the failure the paper describes after Algorithm 1, by spanning whole
 clusters of nearly equal eigenvalues.
 
 Algorithm 1, per sweep over the unconverged i:
-    sigma   = lambda_i * max(1 - eps_i, 0)                 (damped shift)
+    sigma   = lambda_i * max(1 - max(eps_i, floor), 0)     (damped shift; floor:
+              shift_floor, so that |lambda - sigma| stays resolvable)
     v_i    <- (Q - sigma)^-1 v_i                           (FGMRES + two-grid, FP64)
     v_i    <- v_i - sum_{j<i} <v_j|v_i> v_j                 (classical GS, done twice)
     v_i    <- v_i / ||v_i||
@@ -125,9 +126,13 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
         for i in range(n_eig):
             if res[i] <= eps:
                 continue
-            sigma = lam[i] * max(1.0 - res[i], 0.0)
+            # damped shift, with a floor on the damping (keeps the shifted system
+            # solvable by a single precision preconditioner)
+            sigma = lam[i] * max(1.0 - max(res[i], p.get("shift_floor", 0.0)), 0.0)
+            guard = ritz_each_sweep and i >= n_want
+            maxit = min(p.get("guard_maxiter", 8), p["outer_maxiter"]) if guard else p["outer_maxiter"]
             x, info = krylov.fgmres(lambda v: op.Q_sigma(v, sigma), lambda r: B(r, sigma), V[i],
-                                    tol=p["solve_tol"], restart=p["outer_restart"], maxiter=p["outer_maxiter"])
+                                    tol=p["solve_tol"], restart=p["outer_restart"], maxiter=maxit)
             stats["solves"] += 1
             stats["outer_iters"] += info["iters"]
             for _ in range(2):

@@ -31,6 +31,7 @@ class Params(C.Structure):
         ("coarse_restart", C.c_int), ("coarse_maxiter", C.c_int), ("coarse_tol", C.c_double),
         ("solve_tol", C.c_double), ("precision", C.c_int), ("smoother", C.c_int), ("max_sweeps", C.c_int),
         ("n_guard", C.c_int), ("coarse_deflate", C.c_int), ("ritz_each_sweep", C.c_int),
+        ("shift_floor", C.c_double), ("guard_maxiter", C.c_int),
     ]
 
 
@@ -89,6 +90,7 @@ def load():
         "mgeig_eigensolve": (I, [P, I, D, P, P, P, C.POINTER(Stats)]),
         "mgeig_set_timing": (I, [P, I]),
         "mgeig_kernel_times": (I, [P, I, P, P, P, P]),
+        "mgeig_get_stream": (I, [P, C.POINTER(P)]),
         "mgeig_strerror": (C.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -283,6 +285,11 @@ class Context:
         return evals, evecs, resid, dict(st.as_dict(), converged=rc == OK)
 
     # ---- instrumentation -------------------------------------------------
+    def stream(self) -> int:
+        s = C.c_void_p()
+        self._check("mgeig_get_stream", self.lib.mgeig_get_stream(self._h, C.byref(s)))
+        return s.value or 0
+
     def set_timing(self, on: bool):
         self._check("mgeig_set_timing", self.lib.mgeig_set_timing(self._h, 1 if on else 0))
 

@@ -51,6 +51,7 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (p.coarse_restart < 1 || p.coarse_restart > COARSE_PERSISTENT_MAXM || p.coarse_maxiter < 1) return MGEIG_EINVAL;
     if (p.coarse_deflate != 0 && p.coarse_deflate != 1) return MGEIG_EINVAL;
     if (p.ritz_each_sweep != 0 && p.ritz_each_sweep != 1) return MGEIG_EINVAL;
+    if (!(p.shift_floor >= 0 && p.shift_floor < 1) || p.guard_maxiter < 1) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES) return MGEIG_EINVAL;
@@ -101,6 +102,8 @@ void mgeig_default_params(mgeig_params *p) {
     p->n_guard = -1;
     p->coarse_deflate = 1;
     p->ritz_each_sweep = 1;
+    p->shift_floor = 1e-5;
+    p->guard_maxiter = 8;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
@@ -525,6 +528,12 @@ int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms, d
         }
         return (int)K_NCLASS;
     });
+}
+
+int mgeig_get_stream(mgeig_ctx *ctx, void **stream) {
+    if (!ctx || !stream) return MGEIG_EINVAL;
+    *stream = (void *)ctx->c.stream;
+    return MGEIG_OK;
 }
 
 const char *mgeig_strerror(int status) {

@@ -198,7 +198,7 @@ void *mg_test_vector(Ctx &c, int j);
 void mg_rebuild(Ctx &c);   // P and coarse operator from c.W
 void setup(Ctx &c, uint64_t seed);
 void mg_cycle_host(Ctx &c, double sigma, const double *r_dev64_internal, double *z_dev64_internal);
-int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol);
+int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol, int maxiter = 0);
 int eigensolve(Ctx &c, int n_eig, double tol, double *evals, double *evecs_host, double *resid);
 void sap_smooth_f64(Ctx &c, double sigma, const void *b64, void *z64, int cycles);
 void coarse_apply_f64(Ctx &c, double sigma, const void *x64, void *y64);

@@ -600,7 +600,7 @@ void setup(Ctx &c, uint64_t seed) {
 // FGMRES (FP64) with the two-grid preconditioner
 
 template <typename R>
-static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol) {
+static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol, int maxiter) {
     Ctx::Work &w = *c.work;
     const size_t n = c.fine_ncpx();
     const int m = w.outer_m;
@@ -615,7 +615,7 @@ static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol)
     int its = 0;
     bool have_x = false;
     Hess H(m);
-    while (its < c.prm.outer_maxiter) {
+    while (its < maxiter) {
         if (have_x) {
             apply_fine<double>(c, MODE_QSIGMA, sigma, x, V[0]);
             blas_scale<double>(c, cpx<double>(-1), V[0], n);
@@ -630,7 +630,7 @@ static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol)
         if (beta <= tol * bnorm) return MGEIG_OK;
         blas_scale<double>(c, cpx<double>(1.0 / beta), V[0], n);
         H.start(beta);
-        const int mm = std::min(m, c.prm.outer_maxiter - its);
+        const int mm = std::min(m, maxiter - its);
         int k = 0;
         double est = beta;
         for (int j = 0; j < mm; ++j) {
@@ -659,9 +659,11 @@ static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol)
     return MGEIG_ENOCONV;
 }
 
-int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol) {
+int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol, int maxiter) {
     c.st.solves += 1;
-    return c.mixed() ? fgmres_impl<float>(c, sigma, b64, x64, tol) : fgmres_impl<double>(c, sigma, b64, x64, tol);
+    if (maxiter <= 0) maxiter = c.prm.outer_maxiter;
+    return c.mixed() ? fgmres_impl<float>(c, sigma, b64, x64, tol, maxiter)
+                     : fgmres_impl<double>(c, sigma, b64, x64, tol, maxiter);
 }
 
 // ---------------------------------------------------------------------------
@@ -815,10 +817,14 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
         ++sweeps;
         for (int i = 0; i < n_eig; ++i) {
             if (eps[i] <= tol) continue;
-            const double sigma = lam[i] * std::max(1.0 - eps[i], 0.0);
+            // damped shift of Algorithm 1, with a floor on the damping
+            const double sigma = lam[i] * std::max(1.0 - std::max(eps[i], c.prm.shift_floor), 0.0);
             const double t0 = now_s();
             const int outer0 = c.st.outer_iters;
-            int rc = fgmres_solve(c, sigma, M[i], w.x64.p, c.prm.solve_tol);
+            // guard vectors only widen the span: a few FGMRES steps suffice
+            const bool is_guard = c.prm.ritz_each_sweep && i >= n_want;
+            int rc = fgmres_solve(c, sigma, M[i], w.x64.p, c.prm.solve_tol,
+                                  is_guard ? std::min(c.prm.guard_maxiter, c.prm.outer_maxiter) : c.prm.outer_maxiter);
             if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
             if (i > 0) {
                 std::vector<const void *> X(M.begin(), M.begin() + i);
