@@ -356,7 +356,7 @@ DEFAULT_PARAMS = dict(
     gmres_smooth_k=8,
     coarse_tol=5e-2,
     coarse_restart=30,
-    coarse_maxiter=200,
+    coarse_maxiter=64,
     coarse_deflate=True,
     ritz_each_sweep=True,
     shift_floor=1e-5,

@@ -21,7 +21,9 @@ clusters of nearly equal eigenvalues.
 Algorithm 1, per sweep over the unconverged i:
     sigma   = lambda_i * max(1 - max(eps_i, floor), 0)     (damped shift; floor:
               shift_floor, so that |lambda - sigma| stays resolvable)
-    v_i    <- (Q - sigma)^-1 v_i                           (FGMRES + two-grid, FP64)
+    v_i    <- (Q - sigma)^-1 v_i                           (FGMRES + two-grid, FP64, to
+              relative residual min(solve_tol, 0.1 eps / |lambda_i - sigma|): the
+              new vector's eigen-residual is about that tolerance times |lambda_i - sigma|)
     v_i    <- v_i - sum_{j<i} <v_j|v_i> v_j                 (classical GS, done twice)
     v_i    <- v_i / ||v_i||
     update v_i in P (rebuild P and the coarse operator)
@@ -131,8 +133,11 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
             sigma = lam[i] * max(1.0 - max(res[i], p.get("shift_floor", 0.0)), 0.0)
             guard = ritz_each_sweep and i >= n_want
             maxit = min(p.get("guard_maxiter", 8), p["outer_maxiter"]) if guard else p["outer_maxiter"]
+            # inexact solve: the new vector's eigen-residual is about tau |lambda - sigma|
+            dls = abs(lam[i] - sigma)
+            tau = p["solve_tol"] if (guard or dls == 0) else min(p["solve_tol"], max(0.1 * eps / dls, 1e-12))
             x, info = krylov.fgmres(lambda v: op.Q_sigma(v, sigma), lambda r: B(r, sigma), V[i],
-                                    tol=p["solve_tol"], restart=p["outer_restart"], maxiter=maxit)
+                                    tol=tau, restart=p["outer_restart"], maxiter=maxit)
             stats["solves"] += 1
             stats["outer_iters"] += info["iters"]
             for _ in range(2):

@@ -93,7 +93,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->outer_restart = 20;
     p->outer_maxiter = 50;
     p->coarse_restart = 30;
-    p->coarse_maxiter = 200;
+    p->coarse_maxiter = 64;
     p->coarse_tol = 5e-2;
     p->solve_tol = 1e-2;
     p->precision = MGEIG_MIXED;

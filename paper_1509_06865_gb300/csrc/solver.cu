@@ -823,7 +823,12 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             const int outer0 = c.st.outer_iters;
             // guard vectors only widen the span: a few FGMRES steps suffice
             const bool is_guard = c.prm.ritz_each_sweep && i >= n_want;
-            int rc = fgmres_solve(c, sigma, M[i], w.x64.p, c.prm.solve_tol,
+            // inexact solve: the new vector's eigen-residual is about tau |lambda - sigma|,
+            // so tau shrinks to 0.1 tol / |lambda - sigma| near convergence
+            const double dls = std::fabs(lam[i] - sigma);
+            const double tau = (is_guard || dls == 0) ? c.prm.solve_tol
+                                                      : std::min(c.prm.solve_tol, std::max(0.1 * tol / dls, 1e-12));
+            int rc = fgmres_solve(c, sigma, M[i], w.x64.p, tau,
                                   is_guard ? std::min(c.prm.guard_maxiter, c.prm.outer_maxiter) : c.prm.outer_maxiter);
             if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
             if (i > 0) {
