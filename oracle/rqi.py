@@ -33,10 +33,12 @@ starting from lambda_i = 0, eps_i = 1.  P is built from the first N_tv of
 iterated than there are test vectors; updating a v_i beyond the first N_tv leaves P
 unchanged.
 
-After every sweep (with ritz_each_sweep) the iterated vectors are replaced by the
-Ritz vectors of Q in their span, ordered by |theta| (lambda_i = theta_i,
-eps_i = ||Q v_i - theta_i v_i||).  Vector-wise RQI has no view of a cluster of
-nearly equal eigenvalues; the projection separates the vectors inside one.
+After every sweep (with ritz_each_sweep) converged pairs are locked and the
+others are replaced by the Ritz vectors of Q in their span (orthogonal to the
+locked ones); all vectors are kept in |lambda| order.  Vector-wise RQI has no
+view of a cluster of nearly equal eigenvalues; the projection separates the
+vectors inside one, and locking keeps a converged pair from being mixed again
+with inaccurate neighbours.
 """
 from __future__ import annotations
 
@@ -102,9 +104,11 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
         n_eig: int, eps: float, params: dict, max_sweeps: int = 50, log=None, n_want: int = None):
     """Algorithm 1.  Returns (lambda, vectors, eps_i, stats), sorted by |lambda|.
 
-    With ritz_each_sweep the vectors stay in Ritz order and the iteration stops
-    once the n_want lowest pairs are converged (the others only widen the span);
-    otherwise all n_eig must converge."""
+    With ritz_each_sweep: pairs with eps_i <= eps are locked (frozen); after every
+    sweep the unlocked vectors are orthonormalised against the locked ones and
+    replaced by the Ritz vectors of Q in their span, all vectors are kept in
+    |lambda| order, and the iteration stops once the n_want lowest are locked
+    (the others only widen the span).  Without it, all n_eig must converge."""
     p = params
     ritz_each_sweep = p.get("ritz_each_sweep", True)
     n_want = n_eig if n_want is None else n_want
@@ -112,7 +116,6 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
     lam = np.zeros(n_eig)
     res = np.ones(n_eig)
     stats = dict(sweeps=0, solves=0, outer_iters=0)
-
     ntv = B.P.ntv
 
     def rebuild():
@@ -125,6 +128,7 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
     rebuild()
     while unconverged() and stats["sweeps"] < max_sweeps:
         stats["sweeps"] += 1
+        locked = res <= eps
         for i in range(n_eig):
             if res[i] <= eps:
                 continue
@@ -140,10 +144,12 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
                                     tol=tau, restart=p["outer_restart"], maxiter=maxit)
             stats["solves"] += 1
             stats["outer_iters"] += info["iters"]
+            # Gram-Schmidt against v_j, j < i (Algorithm 1) and every locked pair
+            others = [j for j in range(n_eig) if j < i or (ritz_each_sweep and locked[j] and j != i)]
             for _ in range(2):
-                coeff = [np.vdot(V[j], x) for j in range(i)]
-                for j in range(i):
-                    x = x - coeff[j] * V[j]
+                coeff = [np.vdot(V[j], x) for j in others]
+                for c, j in zip(coeff, others):
+                    x = x - c * V[j]
             V[i] = x / dirac.norm(x)
             if i < ntv:
                 rebuild()
@@ -152,10 +158,17 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
                 log(f"sweep {stats['sweeps']} i={i} sigma={sigma:.6e} lambda={lam[i]:.12e} eps={res[i]:.3e} "
                     f"outer={info['iters']}")
         if ritz_each_sweep:
-            R, _ = ritz_rotate(op, np.array(V))
-            V = [v for v in R]
-            for i in range(n_eig):
-                lam[i], res[i] = rayleigh(op, V[i])
+            L = [i for i in range(n_eig) if res[i] <= eps]
+            Uo = [i for i in range(n_eig) if res[i] > eps]
+            if Uo:
+                X = orthonormalise(np.array([V[i] for i in L] + [V[i] for i in Uo]))[len(L):]
+                R, _ = ritz_rotate(op, X)
+                for k, i in enumerate(Uo):
+                    V[i] = R[k]
+                    lam[i], res[i] = rayleigh(op, V[i])
+            order = list(np.lexsort((lam, np.abs(lam))))
+            V = [V[k] for k in order]
+            lam, res = lam[order], res[order]
             rebuild()
     order = np.lexsort((lam, np.abs(lam)))
     return lam[order], np.array(V)[order], res[order], stats

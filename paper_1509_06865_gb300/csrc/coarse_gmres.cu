@@ -16,7 +16,11 @@
 // Grid: G co-resident blocks; block b owns a contiguous slice of coarse rows.
 // One Arnoldi step = the coarse matvec on the owned rows (reading neighbour rows
 // written before the last grid barrier), the deflation projection, two classical
-// Gram-Schmidt passes and a norm: four grid-wide reductions.  Partial sums go to
+// Gram-Schmidt passes and a norm in TWO grid-wide reductions: the deflation
+// coefficients W^dag u and the first pass are reduced together, since
+// <v_i, g5 (u - A W t)> = <g5 v_i, u> - sum_l t_l F_il with F_il = <g5 v_i, A W_l>
+// (row i reduced when v_i is made); the second pass and the norm go together,
+// ||w2||^2 = ||w1||^2 - ||h2||^2.  Partial sums go to
 // a [G][slots] buffer; after each barrier every block adds the G partials in the
 // same order, so all blocks hold bit-identical scalars and run the Givens
 // rotations and the triangular solve redundantly (deterministic, no extra
@@ -32,9 +36,10 @@ namespace mgeig {
 constexpr int CG_THREADS = 1024;
 constexpr int CG_MAXM = COARSE_PERSISTENT_MAXM;   // restart length limit
 constexpr int CG_MAXK = 24;                       // deflation vectors (= max N_tv)
-constexpr int OFF_H1 = 0, OFF_H2 = CG_MAXM + 2, OFF_N = 2 * (CG_MAXM + 2), OFF_P = OFF_N + 2;
+// partial-sum regions of consecutive reductions never overlap
+constexpr int WS = 2 * CG_MAXK + CG_MAXM + 2;     // values of one reduction
+constexpr int OFF_S1 = 0, OFF_S2 = WS, OFF_N = 2 * WS, OFF_P = 2 * WS + 2;
 constexpr int CG_SLOTS = OFF_P + CG_MAXK;
-constexpr int WS = CG_MAXM + 2;                   // per-warp scratch stride
 
 struct CGState {
     unsigned int count;   // barrier arrivals (returns to 0 after every barrier)
@@ -158,6 +163,10 @@ template <typename R>
 __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a) {
     __shared__ double2 wpart[WS];                    // this block's partial sums
     __shared__ double2 h[WS];                        // grid-wide sums after a gather
+    __shared__ double2 F[CG_MAXM * CG_MAXK];         // F_il = <g5 s_i V_i, A W_l>
+    __shared__ double2 h1[CG_MAXM];
+    __shared__ double nsum[CG_THREADS / 32];
+    __shared__ double nrm2s;
     __shared__ double2 Rm[(CG_MAXM + 1) * CG_MAXM];  // rotated Hessenberg, column-major
     __shared__ double cs[CG_MAXM];
     __shared__ double2 sn[CG_MAXM], g[CG_MAXM + 1], y[CG_MAXM];
@@ -281,7 +290,6 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             acc += (double)q.re * q.re + (double)q.im * q.im;
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        __shared__ double nsum[CG_THREADS / 32];
         if (lane == 0) nsum[wp] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -336,22 +344,100 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         bool conv = false;
         for (int j = 0; j < mm; ++j) {
             cpx<R> *w = a.V + (size_t)(j + 1) * a.n;
-            if (!apply_op(Vvec(j), (R)scale[j], w)) return;
-            for (int pass = 0; pass < 2; ++pass) {
-                dots(j + 1, Vvec, [&](int i) { return scale[i]; }, w);
-                if (!reduce(pass == 0 ? OFF_H1 : OFF_H2, j + 1)) return;
-                if (threadIdx.x == 0) {
-                    for (int i = 0; i <= j; ++i) {
-                        double2 &col = Rm[j * (CG_MAXM + 1) + i];
-                        col = pass == 0 ? h[i] : make_double2(col.x + h[i].x, col.y + h[i].y);
-                    }
+            const cpx<R> *vj = Vvec(j);
+            // u = (Q_c - sigma) s_j V_j on the owned rows
+            qmatvec<R>(a, vj, (R)scale[j], w, r0, r1);
+            __syncthreads();
+            // reduction 1: a_l = <W_l, u>, b_i = <g5 s_i V_i, u>, f_l = <g5 s_j V_j, A W_l>
+            dots(k, Wvec, one, w);
+            for (int i = wp; i <= j; i += nw) {
+                const cpx<R> *vi = Vvec(i);
+                double sr = 0, si = 0;
+                for (int t = r0 + lane; t < r1; t += 32) {
+                    cpx<R> pv = g5c(a, t, vi[t]), q = w[t];
+                    sr += (double)pv.re * q.re + (double)pv.im * q.im;
+                    si += (double)pv.re * q.im - (double)pv.im * q.re;
                 }
-                combine(j + 1, Vvec, [&](int i) { return cpx<R>((R)(h[i].x * scale[i]), (R)(h[i].y * scale[i])); }, w,
-                        [](int, cpx<R> ut, cpx<R> s) { return ut - s; });
+                for (int o = 16; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (lane == 0) wpart[k + i] = make_double2(sr * scale[i], si * scale[i]);
             }
-            if (!grid_norm2(w)) return;
+            for (int l = wp; l < k; l += nw) {
+                const cpx<R> *awl = AWvec(l);
+                double sr = 0, si = 0;
+                for (int t = r0 + lane; t < r1; t += 32) {
+                    cpx<R> pv = g5c(a, t, vj[t]), q = awl[t];
+                    sr += (double)pv.re * q.re + (double)pv.im * q.im;
+                    si += (double)pv.re * q.im - (double)pv.im * q.re;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (lane == 0) wpart[k + j + 1 + l] = make_double2(sr * scale[j], si * scale[j]);
+            }
+            if (!reduce(OFF_S1, 2 * k + j + 1)) return;
+            // t = E^-1 a ; F row j ; h1_i = b_i - sum_l F_il t_l
+            for (int l = threadIdx.x; l < k; l += blockDim.x) F[j * CG_MAXK + l] = h[k + j + 1 + l];
+            for (int i = threadIdx.x; i < k; i += blockDim.x) {
+                double sr = 0, si = 0;
+                for (int l = 0; l < k; ++l) {
+                    double2 e = Ei[i * k + l], d = h[l];
+                    sr += e.x * d.x - e.y * d.y;
+                    si += e.x * d.y + e.y * d.x;
+                }
+                tc[i] = make_double2(sr, si);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+                double2 b = h[k + i];
+                for (int l = 0; l < k; ++l) {
+                    double2 f = F[i * CG_MAXK + l], t = tc[l];
+                    b.x -= f.x * t.x - f.y * t.y;
+                    b.y -= f.x * t.y + f.y * t.x;
+                }
+                h1[i] = b;
+                Rm[j * (CG_MAXM + 1) + i] = b;
+            }
+            __syncthreads();
+            // w1 = g5 (u - A W t) - sum_i h1_i s_i V_i
+            combine(k, AWvec, [&](int i) { return cpx<R>((R)tc[i].x, (R)tc[i].y); }, w,
+                    [&](int t, cpx<R> ut, cpx<R> sm) { return g5c(a, t, ut - sm); });
+            combine(j + 1, Vvec, [&](int i) { return cpx<R>((R)(h1[i].x * scale[i]), (R)(h1[i].y * scale[i])); }, w,
+                    [](int, cpx<R> ut, cpx<R> sm) { return ut - sm; });
+            // reduction 2: h2_i = <s_i V_i, w1>, ||w1||^2
+            dots(j + 1, Vvec, [&](int i) { return scale[i]; }, w);
+            {
+                double acc = 0;
+                for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
+                    cpx<R> q = w[t];
+                    acc += (double)q.re * q.re + (double)q.im * q.im;
+                }
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) nsum[wp] = acc;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double s2 = 0;
+                    for (int ww = 0; ww < nw; ++ww) s2 += nsum[ww];
+                    wpart[j + 1] = make_double2(s2, 0);
+                }
+            }
+            if (!reduce(OFF_S2, j + 2)) return;
             if (threadIdx.x == 0) {
-                const double nrm = sqrt(h[0].x);
+                double n2 = h[j + 1].x;
+                for (int i = 0; i <= j; ++i) {
+                    double2 &col = Rm[j * (CG_MAXM + 1) + i];
+                    col = make_double2(col.x + h[i].x, col.y + h[i].y);
+                    n2 -= h[i].x * h[i].x + h[i].y * h[i].y;
+                }
+                nrm2s = n2 > 0 ? n2 : 0.0;
+            }
+            combine(j + 1, Vvec, [&](int i) { return cpx<R>((R)(h[i].x * scale[i]), (R)(h[i].y * scale[i])); }, w,
+                    [](int, cpx<R> ut, cpx<R> sm) { return ut - sm; });
+            if (threadIdx.x == 0) {
+                const double nrm = sqrt(nrm2s);
                 double2 *col = Rm + j * (CG_MAXM + 1);
                 col[j + 1] = make_double2(nrm, 0);
                 for (int i = 0; i < j; ++i) {   // previous rotations

@@ -161,6 +161,7 @@ struct Ctx::Work {
     DevBuf Wc, AWc, Edev, Einv;  // deflation: P^dag w_j, (Q_c - sigma) P^dag w_j, E, E^-1
     DevBuf Mextra, Xall;         // Algorithm 1 vectors beyond the N_tv test vectors; rotation scratch
     std::vector<void *> modes;   // iterated vectors: W[0..N_tv) then the extra ones
+    std::vector<void *> Psrc;    // the N_tv vectors P is built from (W, or the first iterated vectors)
     bool defl_valid = false;
     double defl_sigma = 0;
     std::vector<void *> W, P64, P;
@@ -203,6 +204,7 @@ void mg_alloc(Ctx &c) {
     w.Wc.alloc(cR_bytes(c) * ntv); w.AWc.alloc(cR_bytes(c) * ntv);
     w.Edev.alloc((size_t)ntv * ntv * sizeof(double2)); w.Einv.alloc((size_t)ntv * ntv * sizeof(double2));
     w.defl_valid = false;
+    w.Psrc = w.W;
     c.Dc.alloc((size_t)9 * c.nagg * 4 * ntv * ntv * 2 * c.level_bytes());
 }
 
@@ -488,18 +490,18 @@ void mg_rebuild(Ctx &c) {
     const int ntv = c.prm.n_tv;
     const size_t vb = cR_bytes(c);
     if (c.mixed()) {
-        build_interp<float>(c, (const void *const *)w.W.data(), ntv, w.P.data());
+        build_interp<float>(c, (const void *const *)w.Psrc.data(), ntv, w.P.data());
         build_coarse<float>(c, (const void *const *)w.P.data(), c.Dc.p);
         // coarse images P^dag w_j of the test vectors (the deflation space)
         for (int j = 0; j < ntv; ++j) {
-            convert_f64_to_f32(c, w.W[j], w.rR.p, c.fine_ncpx());
+            convert_f64_to_f32(c, w.Psrc[j], w.rR.p, c.fine_ncpx());
             restrict_vec<float>(c, (const void *const *)w.P.data(), w.rR.p, static_cast<char *>(w.Wc.p) + vb * j);
         }
     } else {
-        build_interp<double>(c, (const void *const *)w.W.data(), ntv, w.P64.data());
+        build_interp<double>(c, (const void *const *)w.Psrc.data(), ntv, w.P64.data());
         build_coarse<double>(c, (const void *const *)w.P.data(), c.Dc.p);
         for (int j = 0; j < ntv; ++j)
-            restrict_vec<double>(c, (const void *const *)w.P.data(), w.W[j], static_cast<char *>(w.Wc.p) + vb * j);
+            restrict_vec<double>(c, (const void *const *)w.P.data(), w.Psrc[j], static_cast<char *>(w.Wc.p) + vb * j);
     }
     w.defl_valid = false;
 }
@@ -508,6 +510,26 @@ void mg_rebuild(Ctx &c) {
 static void orthonormalise(Ctx &c, std::vector<void *> &v, int n) {
     const size_t N = c.fine_ncpx();
     for (int j = 0; j < n; ++j) {
+        if (j > 0) {
+            std::vector<const void *> X(v.begin(), v.begin() + j);
+            for (int pass = 0; pass < 2; ++pass) {
+                blas_multidot<double>(c, X.data(), j, v[j], N, dslot(c, H1));
+                blas_multi_axpy<double>(c, v[j], X.data(), j, dslot(c, H1), -1.0, N);
+            }
+        }
+        blas_norm2<double>(c, v[j], N, dslot(c, HN));
+        fetch(c, HN + 1);
+        const double nrm = std::sqrt(hslot(c, HN)->re);
+        MG_REQUIRE(std::isfinite(nrm) && nrm > 0, MGEIG_EBREAKDOWN);
+        blas_scale<double>(c, cpx<double>(1.0 / nrm), v[j], N);
+    }
+}
+
+// Gram-Schmidt (each step twice) of v[from..n) against all earlier vectors
+static void orthonormalise_from(Ctx &c, std::vector<void *> &v, int from) {
+    const size_t N = c.fine_ncpx();
+    const int n = (int)v.size();
+    for (int j = from; j < n; ++j) {
         if (j > 0) {
             std::vector<const void *> X(v.begin(), v.begin() + j);
             for (int pass = 0; pass < 2; ++pass) {
@@ -561,6 +583,7 @@ template <typename R>
 static void setup_impl(Ctx &c, uint64_t seed) {
     Ctx::Work &w = *c.work;
     const int ntv = c.prm.n_tv;
+    w.Psrc = w.W;
     random_spinors(c, seed, w.Wall.p, ntv, 0x5EED0001u);
     c.setup_seed = seed;
     for (int j = 0; j < ntv; ++j) smooth_random<R>(c, w.W[j]);
@@ -801,13 +824,15 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
     }
     std::vector<void *> &M = w.modes;
     ritz_rotate(c, M, std::max(ntv, n_eig));
+    w.Psrc.assign(M.begin(), M.begin() + ntv);
     mg_rebuild(c);
     std::vector<double> lam(n_eig, 0.0), eps(n_eig, 1.0);
     int sweeps = 0;
-    // with the per-sweep Rayleigh-Ritz step the vectors stay in Ritz order and
-    // only the n_want lowest must converge (the others widen the span)
+    const bool rr = c.prm.ritz_each_sweep != 0;
+    // with the per-sweep Rayleigh-Ritz step converged pairs are locked, the
+    // vectors stay in |lambda| order and only the n_want lowest must converge
     auto unconverged = [&]() {
-        const int n = c.prm.ritz_each_sweep ? n_want : n_eig;
+        const int n = rr ? n_want : n_eig;
         for (int i = 0; i < n; ++i)
             if (eps[i] > tol) return true;
         return false;
@@ -815,6 +840,8 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
     int status = MGEIG_OK;
     while (unconverged() && sweeps < c.prm.max_sweeps) {
         ++sweeps;
+        std::vector<char> locked(n_eig);
+        for (int i = 0; i < n_eig; ++i) locked[i] = eps[i] <= tol;
         for (int i = 0; i < n_eig; ++i) {
             if (eps[i] <= tol) continue;
             // damped shift of Algorithm 1, with a floor on the damping
@@ -822,7 +849,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             const double t0 = now_s();
             const int outer0 = c.st.outer_iters;
             // guard vectors only widen the span: a few FGMRES steps suffice
-            const bool is_guard = c.prm.ritz_each_sweep && i >= n_want;
+            const bool is_guard = rr && i >= n_want;
             // inexact solve: the new vector's eigen-residual is about tau |lambda - sigma|,
             // so tau shrinks to 0.1 tol / |lambda - sigma| near convergence
             const double dls = std::fabs(lam[i] - sigma);
@@ -831,11 +858,14 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             int rc = fgmres_solve(c, sigma, M[i], w.x64.p, tau,
                                   is_guard ? std::min(c.prm.guard_maxiter, c.prm.outer_maxiter) : c.prm.outer_maxiter);
             if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
-            if (i > 0) {
-                std::vector<const void *> X(M.begin(), M.begin() + i);
+            // Gram-Schmidt against v_j, j < i (Algorithm 1), and every locked pair
+            std::vector<const void *> X;
+            for (int j = 0; j < n_eig; ++j)
+                if (j < i || (rr && locked[j] && j != i)) X.push_back(M[j]);
+            if (!X.empty()) {
                 for (int pass = 0; pass < 2; ++pass) {
-                    blas_multidot<double>(c, X.data(), i, w.x64.p, N, dslot(c, H1));
-                    blas_multi_axpy<double>(c, w.x64.p, X.data(), i, dslot(c, H1), -1.0, N);
+                    blas_multidot<double>(c, X.data(), (int)X.size(), w.x64.p, N, dslot(c, H1));
+                    blas_multi_axpy<double>(c, w.x64.p, X.data(), (int)X.size(), dslot(c, H1), -1.0, N);
                 }
             }
             blas_norm2<double>(c, w.x64.p, N, dslot(c, HN));
@@ -856,19 +886,42 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
                         rc == MGEIG_OK ? "ok" : "cap", now_s() - t0);
             }
         }
-        if (c.prm.ritz_each_sweep) {
-            // Rayleigh-Ritz on the iterated vectors: separates nearly equal eigenvalues
-            ritz_rotate(c, M, n_eig);
-            for (int i = 0; i < n_eig; ++i) {
-                auto le = rayleigh(c, M[i]);
-                lam[i] = le.first;
-                eps[i] = le.second;
+        if (rr) {
+            // lock the converged pairs; Rayleigh-Ritz on the others, orthogonal to them
+            std::vector<void *> order;
+            std::vector<int> U;
+            for (int i = 0; i < n_eig; ++i)
+                if (eps[i] <= tol) order.push_back(M[i]);
+                else U.push_back(i);
+            const int nl = (int)order.size();
+            if (!U.empty()) {
+                for (int i : U) order.push_back(M[i]);
+                orthonormalise_from(c, order, nl);
+                std::vector<void *> Mu(order.begin() + nl, order.end());
+                ritz_rotate(c, Mu, (int)Mu.size());
+                for (size_t k = 0; k < U.size(); ++k) {
+                    auto le = rayleigh(c, M[U[k]]);
+                    lam[U[k]] = le.first;
+                    eps[U[k]] = le.second;
+                }
             }
+            // keep every vector in |lambda| order (a permutation of the pointers)
+            std::vector<int> perm(n_eig);
+            std::iota(perm.begin(), perm.end(), 0);
+            std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+                double fa = std::fabs(lam[a]), fb = std::fabs(lam[b]);
+                return fa != fb ? fa < fb : lam[a] < lam[b];
+            });
+            std::vector<void *> M2(n_eig);
+            std::vector<double> l2(n_eig), e2(n_eig);
+            for (int k = 0; k < n_eig; ++k) { M2[k] = M[perm[k]]; l2[k] = lam[perm[k]]; e2[k] = eps[perm[k]]; }
+            for (int k = 0; k < n_eig; ++k) { M[k] = M2[k]; lam[k] = l2[k]; eps[k] = e2[k]; }
+            w.Psrc.assign(M.begin(), M.begin() + ntv);
             mg_rebuild(c);
             if (log_on()) {
                 double mx = 0;
-                for (int i = 0; i < n_eig; ++i) mx = std::max(mx, eps[i]);
-                fprintf(stderr, "mgeig rqi sweep %d rayleigh-ritz max eps %.3e\n", sweeps, mx);
+                for (int i = 0; i < n_want; ++i) mx = std::max(mx, eps[i]);
+                fprintf(stderr, "mgeig rqi sweep %d locked %d max eps (wanted) %.3e\n", sweeps, nl, mx);
             }
         }
     }
