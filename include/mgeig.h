@@ -107,6 +107,15 @@ typedef struct mgeig_params {
                              shift_floor), 0); keeps the shifted system solvable
                              by the single-precision preconditioner              */
     int guard_maxiter;    /* FGMRES step cap for the guard vectors' solves     */
+    double ritz_keep;     /* unconverged pairs with eps <= ritz_keep stay out of
+                             the per-sweep Rayleigh-Ritz step (their own RQI step
+                             converges them; a rotation with rough neighbours of a
+                             nearly equal Ritz value would spoil them again)     */
+    int fine_deflate;     /* 1: inside the eigensolver every shifted solve is
+                             deflated on the fine grid by the iterated vectors Z:
+                             the preconditioner becomes
+                             z = Z E^-1 Z^dag r + B (r - (Q - sigma) Z E^-1 Z^dag r),
+                             E = Z^dag (Q - sigma) Z formed in FP64; 0: plain B */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */

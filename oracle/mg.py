@@ -359,8 +359,10 @@ DEFAULT_PARAMS = dict(
     coarse_maxiter=64,
     coarse_deflate=True,
     ritz_each_sweep=True,
-    shift_floor=1e-5,
+    shift_floor=1e-6,
     guard_maxiter=8,
+    ritz_keep=1e-6,
+    fine_deflate=True,
     outer_restart=20,
     outer_maxiter=50,
     solve_tol=1e-2,

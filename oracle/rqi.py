@@ -23,7 +23,9 @@ Algorithm 1, per sweep over the unconverged i:
               shift_floor, so that |lambda - sigma| stays resolvable)
     v_i    <- (Q - sigma)^-1 v_i                           (FGMRES + two-grid, FP64, to
               relative residual min(solve_tol, 0.1 eps / |lambda_i - sigma|): the
-              new vector's eigen-residual is about that tolerance times |lambda_i - sigma|)
+              new vector's eigen-residual is about that tolerance times |lambda_i - sigma|;
+              with fine_deflate the two-grid preconditioner is deflated by all
+              iterated vectors, see deflated_preconditioner)
     v_i    <- v_i - sum_{j<i} <v_j|v_i> v_j                 (classical GS, done twice)
     v_i    <- v_i / ||v_i||
     update v_i in P (rebuild P and the coarse operator)
@@ -33,9 +35,10 @@ starting from lambda_i = 0, eps_i = 1.  P is built from the first N_tv of
 iterated than there are test vectors; updating a v_i beyond the first N_tv leaves P
 unchanged.
 
-After every sweep (with ritz_each_sweep) converged pairs are locked and the
-others are replaced by the Ritz vectors of Q in their span (orthogonal to the
-locked ones); all vectors are kept in |lambda| order.  Vector-wise RQI has no
+After every sweep (with ritz_each_sweep) converged pairs are locked, nearly
+converged ones (eps_i <= ritz_keep) are only orthonormalised against them, and
+the others are replaced by the Ritz vectors of Q in their span (orthogonal to
+both); all vectors are kept in |lambda| order.  Vector-wise RQI has no
 view of a cluster of nearly equal eigenvalues; the projection separates the
 vectors inside one, and locking keeps a converged pair from being mixed again
 with inaccurate neighbours.
@@ -100,6 +103,24 @@ def rayleigh(op: dirac.WilsonClover, v: np.ndarray):
     return lam, dirac.norm(Qv - lam * v)
 
 
+def deflated_preconditioner(op: dirac.WilsonClover, Z: np.ndarray, B: mg.TwoGrid, sigma: float):
+    """Two-grid preconditioner deflated by the iterated vectors Z (fine_deflate):
+        z = Z E^-1 Z^dag r + B (r - (Q - sigma) Z E^-1 Z^dag r),  E = Z^dag (Q - sigma) Z.
+    span(Z) is solved exactly (a Galerkin projection); the system solved by
+    FGMRES, (Q - sigma) x = v, is unchanged."""
+    shape = Z.shape[1:]
+    Zf = Z.reshape(len(Z), -1)
+    AZ = np.array([op.Q_sigma(z, sigma) for z in Z]).reshape(len(Z), -1)
+    E = Zf.conj() @ AZ.T                      # E_jl = <z_j, (Q - sigma) z_l>
+    Einv = np.linalg.inv(E)
+
+    def apply(r):
+        d = Einv @ (Zf.conj() @ r.reshape(-1))
+        rd = (r.reshape(-1) - AZ.T @ d).reshape(shape)
+        return (Zf.T @ d).reshape(shape) + B(rd, sigma)
+    return apply
+
+
 def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
         n_eig: int, eps: float, params: dict, max_sweeps: int = 50, log=None, n_want: int = None):
     """Algorithm 1.  Returns (lambda, vectors, eps_i, stats), sorted by |lambda|.
@@ -140,7 +161,9 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
             # inexact solve: the new vector's eigen-residual is about tau |lambda - sigma|
             dls = abs(lam[i] - sigma)
             tau = p["solve_tol"] if (guard or dls == 0) else min(p["solve_tol"], max(0.1 * eps / dls, 1e-12))
-            x, info = krylov.fgmres(lambda v: op.Q_sigma(v, sigma), lambda r: B(r, sigma), V[i],
+            precond = (lambda r: B(r, sigma)) if not p.get("fine_deflate", False) else \
+                deflated_preconditioner(op, np.array(V), B, sigma)
+            x, info = krylov.fgmres(lambda v: op.Q_sigma(v, sigma), precond, V[i],
                                     tol=tau, restart=p["outer_restart"], maxiter=maxit)
             stats["solves"] += 1
             stats["outer_iters"] += info["iters"]
@@ -158,13 +181,17 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
                 log(f"sweep {stats['sweeps']} i={i} sigma={sigma:.6e} lambda={lam[i]:.12e} eps={res[i]:.3e} "
                     f"outer={info['iters']}")
         if ritz_each_sweep:
+            keep = p.get("ritz_keep", 0.0)
             L = [i for i in range(n_eig) if res[i] <= eps]
-            Uo = [i for i in range(n_eig) if res[i] > eps]
-            if Uo:
-                X = orthonormalise(np.array([V[i] for i in L] + [V[i] for i in Uo]))[len(L):]
-                R, _ = ritz_rotate(op, X)
-                for k, i in enumerate(Uo):
-                    V[i] = R[k]
+            K = [i for i in range(n_eig) if eps < res[i] <= keep]
+            Uo = [i for i in range(n_eig) if res[i] > max(eps, keep)]
+            if K or Uo:
+                X = orthonormalise(np.array([V[i] for i in L + K + Uo]))[len(L):]
+                R = X[len(K):]
+                if Uo:
+                    R, _ = ritz_rotate(op, R)
+                for k, i in enumerate(K + Uo):
+                    V[i] = X[k] if k < len(K) else R[k - len(K)]
                     lam[i], res[i] = rayleigh(op, V[i])
             order = list(np.lexsort((lam, np.abs(lam))))
             V = [V[k] for k in order]

@@ -52,6 +52,8 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (p.coarse_deflate != 0 && p.coarse_deflate != 1) return MGEIG_EINVAL;
     if (p.ritz_each_sweep != 0 && p.ritz_each_sweep != 1) return MGEIG_EINVAL;
     if (!(p.shift_floor >= 0 && p.shift_floor < 1) || p.guard_maxiter < 1) return MGEIG_EINVAL;
+    if (!(p.ritz_keep >= 0) || !std::isfinite(p.ritz_keep)) return MGEIG_EINVAL;
+    if (p.fine_deflate != 0 && p.fine_deflate != 1) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES) return MGEIG_EINVAL;
@@ -102,8 +104,10 @@ void mgeig_default_params(mgeig_params *p) {
     p->n_guard = -1;
     p->coarse_deflate = 1;
     p->ritz_each_sweep = 1;
-    p->shift_floor = 1e-5;
+    p->shift_floor = 1e-6;
     p->guard_maxiter = 8;
+    p->ritz_keep = 1e-6;
+    p->fine_deflate = 1;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {

@@ -284,6 +284,30 @@ void blas_axpy_to_f64(Ctx &c, cpx<double> a, const void *x, void *y64, size_t n)
     MG_CHECK_LAUNCH();
 }
 
+// y = A x and ys = s * y for a small row-major k x k matrix A (k <= 64), one
+// thread per row; A, x, y and ys live on the device (no host round trip)
+__global__ void small_gemv_kernel(const double2 *__restrict__ A, int k, const double2 *__restrict__ x, double s,
+                                  double2 *__restrict__ y, double2 *__restrict__ ys) {
+    const int i = threadIdx.x;
+    if (i >= k) return;
+    double re = 0, im = 0;
+    for (int l = 0; l < k; ++l) {
+        const double2 a = A[(size_t)i * k + l], b = x[l];
+        re = fma(a.x, b.x, re); re = fma(-a.y, b.y, re);
+        im = fma(a.x, b.y, im); im = fma(a.y, b.x, im);
+    }
+    y[i] = make_double2(re, im);
+    ys[i] = make_double2(s * re, s * im);
+}
+
+void small_gemv(Ctx &c, const cpx<double> *A, int k, const cpx<double> *x, double s, cpx<double> *y, cpx<double> *ys) {
+    MG_REQUIRE(k >= 1 && k <= 64, MGEIG_EINVAL);
+    TimeScope ts(c.timer, K_BLAS_F64, (double)k * (k + 3) * 16);
+    small_gemv_kernel<<<1, 64, 0, c.stream>>>(reinterpret_cast<const double2 *>(A), k, reinterpret_cast<const double2 *>(x),
+                                              s, reinterpret_cast<double2 *>(y), reinterpret_cast<double2 *>(ys));
+    MG_CHECK_LAUNCH();
+}
+
 #define INST(R)                                                                                             \
     template void blas_multidot<R>(Ctx &, const void *const *, int, const void *, size_t, cpx<double> *);    \
     template void blas_multi_axpy<R>(Ctx &, void *, const void *const *, int, const cpx<double> *, double, size_t); \

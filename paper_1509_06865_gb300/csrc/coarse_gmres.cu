@@ -49,6 +49,10 @@ struct CGState {
 };
 static_assert(sizeof(CGState) == 16, "CGState lives in one reduction slot");
 
+template <typename R> struct Pod2;
+template <> struct Pod2<float> { using T = float2; };
+template <> struct Pod2<double> { using T = double2; };
+
 template <typename R>
 struct CGArgs {
     int nagg, ntv, n;              // coarse sites, test vectors, rows = nagg * 2 ntv
@@ -62,7 +66,7 @@ struct CGArgs {
     int k;                         // deflation vectors (0: none)
     const cpx<R> *W, *AW;          // k x n each
     const double2 *Einv;           // k x k, row-major
-    double2 *partial;              // [G][CG_SLOTS]
+    typename Pod2<R>::T *partial;  // [G][CG_SLOTS]
     CGState *st;
     int m, maxiter;
     double tol;
@@ -107,8 +111,9 @@ __device__ __forceinline__ cpx<double> ldcg(const cpx<double> *p) {
 }
 
 // u[t] = ((Q_c - sigma)(s v))[t] = ((gamma5^c D_c - sigma)(s v))[t] for the rows
-// t in [r0, r1); a group of TPR consecutive threads shares one row (its lanes
-// take the nine hop directions in turn) and reduces with shuffles.
+// t in [r0, r1); a group of TPR consecutive threads shares one row: lane q takes
+// the columns j = q (mod TPR) of all nine hop blocks, and the group reduces with
+// shuffles.
 constexpr int TPR = 8;
 
 template <typename R>
@@ -117,12 +122,13 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
     const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
     for (int tb = r0; tb < r1; tb += ngrp) {
         const int t = tb + grp;
-        cpx<R> acc0, acc1, acc2, acc3;
+        cpx<R> acc0, acc1;
         if (t < r1) {
             const int site = t / n2, row = t % n2;
             int ac[4], rem = site;
             for (int mu = 0; mu < 4; ++mu) { ac[mu] = rem % a.cd[mu]; rem /= a.cd[mu]; }
-            for (int d = q; d < 9; d += TPR) {
+#pragma unroll 3
+            for (int d = 0; d < 9; ++d) {
                 int nb = site;
                 if (d > 0) {
                     const int mu = (d - 1) / 2, step = (d & 1) ? 1 : -1;
@@ -132,17 +138,15 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
                 }
                 const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
                 const cpx<R> *xb = v + (size_t)nb * n2;
-                int j = 0;
-                for (; j + 3 < n2; j += 4) {
+                int j = q;
+                for (; j + TPR < n2; j += 2 * TPR) {
                     cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
-                    cmac(acc1, blk[(size_t)(j + 1) * n2], ldcg(xb + j + 1));
-                    cmac(acc2, blk[(size_t)(j + 2) * n2], ldcg(xb + j + 2));
-                    cmac(acc3, blk[(size_t)(j + 3) * n2], ldcg(xb + j + 3));
+                    cmac(acc1, blk[(size_t)(j + TPR) * n2], ldcg(xb + j + TPR));
                 }
-                for (; j < n2; ++j) cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+                if (j < n2) cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
             }
         }
-        cpx<R> acc = (acc0 + acc1) + (acc2 + acc3);
+        cpx<R> acc = acc0 + acc1;
         for (int o = 1; o < TPR; o <<= 1) {
             acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
             acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
@@ -159,20 +163,26 @@ __device__ __forceinline__ cpx<R> g5c(const CGArgs<R> &a, int t, cpx<R> v) {
     return (t % (2 * a.ntv)) >= a.ntv ? -v : v;
 }
 
+// Scalars (partial sums, Hessenberg matrix, Givens rotations, E^-1) are kept in
+// the solver's own precision R: FP32 in the mixed-precision preconditioner,
+// where FP64 arithmetic (1/64 of the FP32 rate on this part) held most warps at
+// block barriers, FP64 in the all-FP64 path.
 template <typename R>
 __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a) {
-    __shared__ double2 wpart[WS];                    // this block's partial sums
-    __shared__ double2 h[WS];                        // grid-wide sums after a gather
-    __shared__ double2 F[CG_MAXM * CG_MAXK];         // F_il = <g5 s_i V_i, A W_l>
-    __shared__ double2 h1[CG_MAXM];
-    __shared__ double nsum[CG_THREADS / 32];
-    __shared__ double nrm2s;
-    __shared__ double2 Rm[(CG_MAXM + 1) * CG_MAXM];  // rotated Hessenberg, column-major
-    __shared__ double cs[CG_MAXM];
-    __shared__ double2 sn[CG_MAXM], g[CG_MAXM + 1], y[CG_MAXM];
-    __shared__ double scale[CG_MAXM + 1];
-    __shared__ double2 Ei[CG_MAXK * CG_MAXK], t0[CG_MAXK], tc[CG_MAXK];
-    __shared__ double bnorm, beta;
+    using P = typename Pod2<R>::T;
+    auto P2 = [](R x, R y) { return P{x, y}; };
+    __shared__ P wpart[WS];                    // this block's partial sums
+    __shared__ P h[WS];                        // grid-wide sums after a gather
+    __shared__ P F[CG_MAXM * CG_MAXK];         // F_il = <g5 s_i V_i, A W_l>
+    __shared__ P h1[CG_MAXM];
+    __shared__ R nsum[CG_THREADS / 32];
+    __shared__ R nrm2s;
+    __shared__ P Rm[(CG_MAXM + 1) * CG_MAXM];  // rotated Hessenberg, column-major
+    __shared__ R cs[CG_MAXM];
+    __shared__ P sn[CG_MAXM], g[CG_MAXM + 1], y[CG_MAXM];
+    __shared__ R scale[CG_MAXM + 1];
+    __shared__ P Ei[CG_MAXK * CG_MAXK], t0[CG_MAXK], tc[CG_MAXK];
+    __shared__ R bnorm, beta;
     __shared__ int stop;
     const unsigned int G = gridDim.x;
     const int nw = CG_THREADS / 32;
@@ -180,11 +190,11 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     const int rows_per_block = (a.n + G - 1) / G;
     const int r0 = blockIdx.x * rows_per_block;
     const int r1 = min(a.n, r0 + rows_per_block);
-    double2 *mypart = a.partial + (size_t)blockIdx.x * CG_SLOTS;
+    P *mypart = a.partial + (size_t)blockIdx.x * CG_SLOTS;
     const int k = a.k;
 
-    for (int i = threadIdx.x; i < k * k; i += blockDim.x) Ei[i] = a.Einv[i];
-    if (threadIdx.x < CG_MAXK) { tc[threadIdx.x] = make_double2(0, 0); t0[threadIdx.x] = make_double2(0, 0); }
+    for (int i = threadIdx.x; i < k * k; i += blockDim.x) Ei[i] = P2((R)a.Einv[i].x, (R)a.Einv[i].y);
+    if (threadIdx.x < CG_MAXK) { tc[threadIdx.x] = P2(0, 0); t0[threadIdx.x] = P2(0, 0); }
     __syncthreads();
 
     // wpart[i] = sc_i <X_i, u> over the owned rows, i < cnt: warp i takes value i,
@@ -192,17 +202,17 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     auto dots = [&](int cnt, auto vec, auto sc, const cpx<R> *u) {
         for (int i = wp; i < cnt; i += nw) {
             const cpx<R> *xi = vec(i);
-            double sr = 0, si = 0;
+            R sr = 0, si = 0;
             for (int t = r0 + lane; t < r1; t += 32) {
                 cpx<R> p = xi[t], q = u[t];
-                sr += (double)p.re * q.re + (double)p.im * q.im;
-                si += (double)p.re * q.im - (double)p.im * q.re;
+                sr += p.re * q.re + p.im * q.im;
+                si += p.re * q.im - p.im * q.re;
             }
             for (int o = 16; o > 0; o >>= 1) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 si += __shfl_xor_sync(0xffffffffu, si, o);
             }
-            if (lane == 0) wpart[i] = make_double2(sr * sc(i), si * sc(i));
+            if (lane == 0) wpart[i] = P2(sr * sc(i), si * sc(i));
         }
     };
     // publish wpart[0..cnt) to this block's partial slots, barrier, h = grid sums
@@ -211,16 +221,16 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) mypart[off + i] = wpart[i];
         if (!grid_sync(a.st, G, a.timeout)) return false;
         for (int i = wp; i < cnt; i += nw) {
-            double sr = 0, si = 0;
+            R sr = 0, si = 0;
             for (unsigned int q = lane; q < G; q += 32) {
-                double2 p = __ldcg(a.partial + (size_t)q * CG_SLOTS + off + i);
+                P p = __ldcg(a.partial + (size_t)q * CG_SLOTS + off + i);
                 sr += p.x; si += p.y;
             }
             for (int o = 16; o > 0; o >>= 1) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 si += __shfl_xor_sync(0xffffffffu, si, o);
             }
-            if (lane == 0) h[i] = make_double2(sr, si);
+            if (lane == 0) h[i] = P2(sr, si);
         }
         __syncthreads();
         return true;
@@ -248,7 +258,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         }
         __syncthreads();
     };
-    auto one = [](int) { return 1.0; };
+    auto one = [](int) { return R(1); };
     auto Wvec = [&](int i) { return a.W + (size_t)i * a.n; };
     auto AWvec = [&](int i) { return a.AW + (size_t)i * a.n; };
     auto Vvec = [&](int i) { return a.V + (size_t)i * a.n; };
@@ -258,13 +268,13 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         dots(k, Wvec, one, u);
         if (!reduce(OFF_P, k)) return false;
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
-            double sr = 0, si = 0;
+            R sr = 0, si = 0;
             for (int l = 0; l < k; ++l) {
-                double2 e = Ei[i * k + l], d = h[l];
+                P e = Ei[i * k + l], d = h[l];
                 sr += e.x * d.x - e.y * d.y;
                 si += e.x * d.y + e.y * d.x;
             }
-            tc[i] = make_double2(sr, si);
+            tc[i] = P2(sr, si);
         }
         __syncthreads();
         return true;
@@ -284,18 +294,18 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     };
     // h[0] = ||v||^2 over the grid
     auto grid_norm2 = [&](const cpx<R> *v) -> bool {
-        double acc = 0;
+        R acc = 0;
         for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
             cpx<R> q = v[t];
-            acc += (double)q.re * q.re + (double)q.im * q.im;
+            acc += q.re * q.re + q.im * q.im;
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) nsum[wp] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double s2 = 0;
+            R s2 = 0;
             for (int w = 0; w < nw; ++w) s2 += nsum[w];
-            wpart[0] = make_double2(s2, 0);
+            wpart[0] = P2(s2, 0);
         }
         return reduce(OFF_N, 1);
     };
@@ -316,7 +326,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     project_g5(a.rhs);
     if (threadIdx.x == 0) stop = !(bnorm > 0) || !isfinite(bnorm);
     __syncthreads();
-    const double tol_abs = a.tol * bnorm;
+    const R tol_abs = (R)a.tol * bnorm;
     int its = 0;
     bool have_x = false;
     while (!stop && its < a.maxiter) {
@@ -333,9 +343,9 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             beta = sqrt(h[0].x);
             stop = !(beta > tol_abs) || !isfinite(beta);
             if (!isfinite(beta)) atomicExch(&a.st->status, 2);
-            scale[0] = beta > 0 ? 1.0 / beta : 0.0;
-            g[0] = make_double2(beta, 0);
-            for (int i = 1; i <= CG_MAXM; ++i) g[i] = make_double2(0, 0);
+            scale[0] = beta > 0 ? R(1) / beta : R(0);
+            g[0] = P2(beta, 0);
+            for (int i = 1; i <= CG_MAXM; ++i) g[i] = P2(0, 0);
         }
         __syncthreads();
         if (stop) break;
@@ -352,49 +362,49 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             dots(k, Wvec, one, w);
             for (int i = wp; i <= j; i += nw) {
                 const cpx<R> *vi = Vvec(i);
-                double sr = 0, si = 0;
+                R sr = 0, si = 0;
                 for (int t = r0 + lane; t < r1; t += 32) {
                     cpx<R> pv = g5c(a, t, vi[t]), q = w[t];
-                    sr += (double)pv.re * q.re + (double)pv.im * q.im;
-                    si += (double)pv.re * q.im - (double)pv.im * q.re;
+                    sr += pv.re * q.re + pv.im * q.im;
+                    si += pv.re * q.im - pv.im * q.re;
                 }
                 for (int o = 16; o > 0; o >>= 1) {
                     sr += __shfl_xor_sync(0xffffffffu, sr, o);
                     si += __shfl_xor_sync(0xffffffffu, si, o);
                 }
-                if (lane == 0) wpart[k + i] = make_double2(sr * scale[i], si * scale[i]);
+                if (lane == 0) wpart[k + i] = P2(sr * scale[i], si * scale[i]);
             }
             for (int l = wp; l < k; l += nw) {
                 const cpx<R> *awl = AWvec(l);
-                double sr = 0, si = 0;
+                R sr = 0, si = 0;
                 for (int t = r0 + lane; t < r1; t += 32) {
                     cpx<R> pv = g5c(a, t, vj[t]), q = awl[t];
-                    sr += (double)pv.re * q.re + (double)pv.im * q.im;
-                    si += (double)pv.re * q.im - (double)pv.im * q.re;
+                    sr += pv.re * q.re + pv.im * q.im;
+                    si += pv.re * q.im - pv.im * q.re;
                 }
                 for (int o = 16; o > 0; o >>= 1) {
                     sr += __shfl_xor_sync(0xffffffffu, sr, o);
                     si += __shfl_xor_sync(0xffffffffu, si, o);
                 }
-                if (lane == 0) wpart[k + j + 1 + l] = make_double2(sr * scale[j], si * scale[j]);
+                if (lane == 0) wpart[k + j + 1 + l] = P2(sr * scale[j], si * scale[j]);
             }
             if (!reduce(OFF_S1, 2 * k + j + 1)) return;
             // t = E^-1 a ; F row j ; h1_i = b_i - sum_l F_il t_l
             for (int l = threadIdx.x; l < k; l += blockDim.x) F[j * CG_MAXK + l] = h[k + j + 1 + l];
             for (int i = threadIdx.x; i < k; i += blockDim.x) {
-                double sr = 0, si = 0;
+                R sr = 0, si = 0;
                 for (int l = 0; l < k; ++l) {
-                    double2 e = Ei[i * k + l], d = h[l];
+                    P e = Ei[i * k + l], d = h[l];
                     sr += e.x * d.x - e.y * d.y;
                     si += e.x * d.y + e.y * d.x;
                 }
-                tc[i] = make_double2(sr, si);
+                tc[i] = P2(sr, si);
             }
             __syncthreads();
             for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-                double2 b = h[k + i];
+                P b = h[k + i];
                 for (int l = 0; l < k; ++l) {
-                    double2 f = F[i * CG_MAXK + l], t = tc[l];
+                    P f = F[i * CG_MAXK + l], t = tc[l];
                     b.x -= f.x * t.x - f.y * t.y;
                     b.y -= f.x * t.y + f.y * t.x;
                 }
@@ -410,63 +420,63 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             // reduction 2: h2_i = <s_i V_i, w1>, ||w1||^2
             dots(j + 1, Vvec, [&](int i) { return scale[i]; }, w);
             {
-                double acc = 0;
+                R acc = 0;
                 for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
                     cpx<R> q = w[t];
-                    acc += (double)q.re * q.re + (double)q.im * q.im;
+                    acc += q.re * q.re + q.im * q.im;
                 }
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 if (lane == 0) nsum[wp] = acc;
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    double s2 = 0;
+                    R s2 = 0;
                     for (int ww = 0; ww < nw; ++ww) s2 += nsum[ww];
-                    wpart[j + 1] = make_double2(s2, 0);
+                    wpart[j + 1] = P2(s2, 0);
                 }
             }
             if (!reduce(OFF_S2, j + 2)) return;
             if (threadIdx.x == 0) {
-                double n2 = h[j + 1].x;
+                R n2 = h[j + 1].x;
                 for (int i = 0; i <= j; ++i) {
-                    double2 &col = Rm[j * (CG_MAXM + 1) + i];
-                    col = make_double2(col.x + h[i].x, col.y + h[i].y);
+                    P &col = Rm[j * (CG_MAXM + 1) + i];
+                    col = P2(col.x + h[i].x, col.y + h[i].y);
                     n2 -= h[i].x * h[i].x + h[i].y * h[i].y;
                 }
-                nrm2s = n2 > 0 ? n2 : 0.0;
+                nrm2s = n2 > 0 ? n2 : R(0);
             }
             combine(j + 1, Vvec, [&](int i) { return cpx<R>((R)(h[i].x * scale[i]), (R)(h[i].y * scale[i])); }, w,
                     [](int, cpx<R> ut, cpx<R> sm) { return ut - sm; });
             if (threadIdx.x == 0) {
-                const double nrm = sqrt(nrm2s);
-                double2 *col = Rm + j * (CG_MAXM + 1);
-                col[j + 1] = make_double2(nrm, 0);
+                const R nrm = sqrt(nrm2s);
+                P *col = Rm + j * (CG_MAXM + 1);
+                col[j + 1] = P2(nrm, 0);
                 for (int i = 0; i < j; ++i) {   // previous rotations
-                    double2 p = col[i], q = col[i + 1], sv = sn[i];
-                    col[i] = make_double2(cs[i] * p.x + (sv.x * q.x - sv.y * q.y), cs[i] * p.y + (sv.x * q.y + sv.y * q.x));
-                    col[i + 1] = make_double2(cs[i] * q.x - (sv.x * p.x + sv.y * p.y), cs[i] * q.y - (sv.x * p.y - sv.y * p.x));
+                    P p = col[i], q = col[i + 1], sv = sn[i];
+                    col[i] = P2(cs[i] * p.x + (sv.x * q.x - sv.y * q.y), cs[i] * p.y + (sv.x * q.y + sv.y * q.x));
+                    col[i + 1] = P2(cs[i] * q.x - (sv.x * p.x + sv.y * p.y), cs[i] * q.y - (sv.x * p.y - sv.y * p.x));
                 }
-                double2 p = col[j], q = col[j + 1];
-                double ap = hypot(p.x, p.y), aq = hypot(q.x, q.y);
-                double c, sr, si;
+                P p = col[j], q = col[j + 1];
+                R ap = hypot(p.x, p.y), aq = hypot(q.x, q.y);
+                R c, sr, si;
                 if (aq == 0) { c = 1; sr = 0; si = 0; }
                 else if (ap == 0) { c = 0; sr = 1; si = 0; }
                 else {
-                    double tt = hypot(ap, aq);
+                    R tt = hypot(ap, aq);
                     c = ap / tt;
-                    double ur = p.x / ap, ui = p.y / ap;          // s = (p/|p|) conj(q) / t
+                    R ur = p.x / ap, ui = p.y / ap;          // s = (p/|p|) conj(q) / t
                     sr = (ur * q.x + ui * q.y) / tt;
                     si = (ui * q.x - ur * q.y) / tt;
                 }
                 cs[j] = c;
-                sn[j] = make_double2(sr, si);
-                col[j] = make_double2(c * p.x + (sr * q.x - si * q.y), c * p.y + (sr * q.y + si * q.x));
-                col[j + 1] = make_double2(0, 0);
-                double2 gj = g[j];
-                g[j + 1] = make_double2(-(sr * gj.x + si * gj.y), -(sr * gj.y - si * gj.x));
-                g[j] = make_double2(c * gj.x, c * gj.y);
-                const double est = hypot(g[j + 1].x, g[j + 1].y);
+                sn[j] = P2(sr, si);
+                col[j] = P2(c * p.x + (sr * q.x - si * q.y), c * p.y + (sr * q.y + si * q.x));
+                col[j + 1] = P2(0, 0);
+                P gj = g[j];
+                g[j + 1] = P2(-(sr * gj.x + si * gj.y), -(sr * gj.y - si * gj.x));
+                g[j] = P2(c * gj.x, c * gj.y);
+                const R est = hypot(g[j + 1].x, g[j + 1].y);
                 if (!isfinite(nrm) || !isfinite(est)) atomicExch(&a.st->status, 2);
-                scale[j + 1] = nrm > 0 ? 1.0 / nrm : 0.0;
+                scale[j + 1] = nrm > 0 ? R(1) / nrm : R(0);
                 stop = (est <= tol_abs) || nrm == 0 || !isfinite(est);
             }
             __syncthreads();
@@ -475,16 +485,16 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         }
         if (threadIdx.x == 0) {   // y = R^-1 g
             for (int i = kk - 1; i >= 0; --i) {
-                double2 sacc = g[i];
+                P sacc = g[i];
                 for (int l = i + 1; l < kk; ++l) {
-                    double2 r = Rm[l * (CG_MAXM + 1) + i], yl = y[l];
+                    P r = Rm[l * (CG_MAXM + 1) + i], yl = y[l];
                     sacc.x -= r.x * yl.x - r.y * yl.y;
                     sacc.y -= r.x * yl.y + r.y * yl.x;
                 }
-                double2 d = Rm[i * (CG_MAXM + 1) + i];
-                double dd = d.x * d.x + d.y * d.y;
-                y[i] = dd > 0 ? make_double2((sacc.x * d.x + sacc.y * d.y) / dd, (sacc.y * d.x - sacc.x * d.y) / dd)
-                              : make_double2(0, 0);
+                P d = Rm[i * (CG_MAXM + 1) + i];
+                R dd = d.x * d.x + d.y * d.y;
+                y[i] = dd > 0 ? P2((sacc.x * d.x + sacc.y * d.y) / dd, (sacc.y * d.x - sacc.x * d.y) / dd)
+                              : P2(0, 0);
             }
         }
         __syncthreads();
@@ -539,7 +549,7 @@ void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, con
     a.W = static_cast<const cpx<R> *>(B.W);
     a.AW = static_cast<const cpx<R> *>(B.AW);
     a.Einv = static_cast<const double2 *>(B.Einv);
-    a.partial = B.partial->as<double2>();
+    a.partial = B.partial->as<typename Pod2<R>::T>();
     a.st = static_cast<CGState *>(B.state);
     a.m = m;
     a.maxiter = c.prm.coarse_maxiter;

@@ -108,6 +108,7 @@ constexpr int MAX_ITERATED = 64;   // vectors iterated by Algorithm 1
 // Results of reductions land in device memory (cpx<double>); *_host variants sync.
 template <typename R> void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n, cpx<double> *d_out);
 template <typename R> void blas_multi_axpy(Ctx &c, void *y, const void *const *X, int k, const cpx<double> *d_coef, double sign, size_t n);
+void small_gemv(Ctx &c, const cpx<double> *A, int k, const cpx<double> *x, double s, cpx<double> *y, cpx<double> *ys);
 template <typename R> void blas_norm2(Ctx &c, const void *x, size_t n, cpx<double> *d_out);
 template <typename R> void blas_axpy(Ctx &c, cpx<double> a, const void *x, void *y, size_t n);
 template <typename R> void blas_scale(Ctx &c, cpx<double> a, void *x, size_t n);

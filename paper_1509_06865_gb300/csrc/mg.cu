@@ -468,7 +468,7 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
     cpx<R> *rho = reinterpret_cast<cpx<R> *>(smem_raw);       // [vol][12]
     float4 *slink = reinterpret_cast<float4 *>(smem_raw + (size_t)B.vol * 12 * sizeof(cpx<R>));   // [vol][4][3]
     constexpr bool stage = sizeof(R) == 4;
-    __shared__ double red[3 * 32];
+    __shared__ R red[3 * 32];   // MR step sums, in the kernel's precision
     const int b = blockIdx.x;
     {
         int r = b, bsum = 0;
@@ -527,7 +527,7 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
     for (int it = 0; it < mr_iters; ++it) {
         // q = D_sigma restricted to the block (Dirichlet) applied to rho
         cpx<R> q[12], rl[12];
-        double qr_re = 0, qr_im = 0, qq = 0;
+        R qr_re = 0, qr_im = 0, qq = 0;
         if (active) {
             cpx<R> up[6], lo[6];
 #pragma unroll
@@ -569,9 +569,9 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
             }
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
-                qr_re += (double)q[k].re * rl[k].re + (double)q[k].im * rl[k].im;
-                qr_im += (double)q[k].re * rl[k].im - (double)q[k].im * rl[k].re;
-                qq += (double)q[k].re * q[k].re + (double)q[k].im * q[k].im;
+                qr_re += q[k].re * rl[k].re + q[k].im * rl[k].im;
+                qr_im += q[k].re * rl[k].im - q[k].im * rl[k].re;
+                qq += q[k].re * q[k].re + q[k].im * q[k].im;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -581,9 +581,9 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
         }
         if (lane == 0) { red[3 * w] = qr_re; red[3 * w + 1] = qr_im; red[3 * w + 2] = qq; }
         __syncthreads();   // all reads of rho for this step are done, partials visible
-        double A_re = 0, A_im = 0, A_qq = 0;
+        R A_re = 0, A_im = 0, A_qq = 0;
         for (int i = 0; i < nw; ++i) { A_re += red[3 * i]; A_im += red[3 * i + 1]; A_qq += red[3 * i + 2]; }
-        const cpx<R> alpha = A_qq > 0 ? cpx<R>((R)(A_re / A_qq), (R)(A_im / A_qq)) : cpx<R>();
+        const cpx<R> alpha = A_qq > 0 ? cpx<R>(A_re / A_qq, A_im / A_qq) : cpx<R>();
         if (active) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) {

@@ -165,6 +165,13 @@ struct Ctx::Work {
     bool defl_valid = false;
     double defl_sigma = 0;
     std::vector<void *> W, P64, P;
+    // fine-grid deflation of the eigensolver's shifted solves by the iterated vectors
+    DevBuf QZ64all;              // Q z_j (FP64)
+    DevBuf ZRall, QZRall;        // level-precision copies of z_j and Q z_j (mixed only)
+    DevBuf fdEinv, fdCoef;       // (Z^dag (Q - sigma) Z)^-1; coefficients c, d = E^-1 c, -sigma d
+    std::vector<void *> QZ64, fdZ, fdQZ;   // FP64 Q z_j; level-precision z_j and Q z_j
+    std::vector<cpx<double>> Gz, Hz;       // Z^dag Z and Z^dag Q Z (row-major, k x k)
+    int fd_k = 0;                          // vectors of the active deflation (0: off)
 };
 
 static size_t f64_bytes(const Ctx &c) { return c.fine_ncpx() * sizeof(double2); }
@@ -221,6 +228,7 @@ void mg_free(Ctx &c) {
     w.cgV.free(); w.cgRhs.free(); w.cgP.free();
     w.Wc.free(); w.AWc.free(); w.Edev.free(); w.Einv.free();
     w.Mextra.free(); w.Xall.free();
+    w.QZ64all.free(); w.ZRall.free(); w.QZRall.free(); w.fdEinv.free(); w.fdCoef.free();
     delete c.work;
     c.work = nullptr;
     c.Dc.free();
@@ -620,6 +628,116 @@ void setup(Ctx &c, uint64_t seed) {
 }
 
 // ---------------------------------------------------------------------------
+// Fine-grid deflation of the shifted solves of Algorithm 1 by the iterated
+// vectors Z = [z_1 .. z_k] (the current eigenvector approximations and guards).
+// Near an eigenvalue, Q - sigma is nearly singular on the eigenvector being
+// refined and, inside a cluster, on its neighbours; only N_tv of them are in P.
+// With E = Z^dag (Q - sigma) Z (FP64, from the FP64 products Z^dag Z and
+// Z^dag Q Z) the preconditioner of the outer FGMRES becomes
+//     z = Z E^-1 Z^dag r + B (r - (Q - sigma) Z E^-1 Z^dag r),
+// so span(Z) is solved exactly (Galerkin) and the two-grid method B only sees
+// the deflated residual.  The iteration still solves (Q - sigma) x = v.
+
+// Q z_i, its level-precision copies and row/column i of Z^dag Z, Z^dag Q Z
+static void fdefl_update(Ctx &c, const std::vector<void *> &M, int i) {
+    Ctx::Work &w = *c.work;
+    const size_t N = c.fine_ncpx();
+    const int k = w.fd_k;
+    apply_fine<double>(c, MODE_QSIGMA, 0.0, M[i], w.QZ64[i]);
+    std::vector<const void *> X(M.begin(), M.begin() + k);
+    blas_multidot<double>(c, X.data(), k, M[i], N, dslot(c, H1));
+    blas_multidot<double>(c, X.data(), k, w.QZ64[i], N, dslot(c, H2));
+    fetch(c, H2 + k);
+    for (int j = 0; j < k; ++j) {
+        const cpx<double> g = *hslot(c, H1 + j), h = *hslot(c, H2 + j);   // <z_j, z_i>, <z_j, Q z_i>
+        w.Gz[(size_t)j * k + i] = g;
+        w.Gz[(size_t)i * k + j] = conj(g);
+        w.Hz[(size_t)j * k + i] = h;
+        w.Hz[(size_t)i * k + j] = conj(h);   // Q is Hermitian
+    }
+    w.Gz[(size_t)i * k + i] = cpx<double>(w.Gz[(size_t)i * k + i].re);
+    w.Hz[(size_t)i * k + i] = cpx<double>(w.Hz[(size_t)i * k + i].re);
+    if (c.mixed()) {
+        convert_f64_to_f32(c, M[i], w.fdZ[i], N);
+        convert_f64_to_f32(c, w.QZ64[i], w.fdQZ[i], N);
+    } else {
+        w.fdZ[i] = M[i];
+        w.fdQZ[i] = w.QZ64[i];
+    }
+}
+
+static void fdefl_all(Ctx &c, const std::vector<void *> &M) {
+    for (int i = 0; i < c.work->fd_k; ++i) fdefl_update(c, M, i);
+}
+
+static void fdefl_begin(Ctx &c, const std::vector<void *> &M, int k) {
+    Ctx::Work &w = *c.work;
+    w.fd_k = 0;
+    if (!c.prm.fine_deflate) return;
+    MG_REQUIRE(k >= 1 && k <= MAX_ITERATED, MGEIG_EINVAL);
+    w.QZ64all.alloc(f64_bytes(c) * k);
+    w.QZ64.resize(k);
+    w.fdZ.resize(k);
+    w.fdQZ.resize(k);
+    for (int j = 0; j < k; ++j) w.QZ64[j] = static_cast<char *>(w.QZ64all.p) + f64_bytes(c) * j;
+    if (c.mixed()) {
+        w.ZRall.alloc(fR_bytes(c) * k);
+        w.QZRall.alloc(fR_bytes(c) * k);
+        for (int j = 0; j < k; ++j) {
+            w.fdZ[j] = static_cast<char *>(w.ZRall.p) + fR_bytes(c) * j;
+            w.fdQZ[j] = static_cast<char *>(w.QZRall.p) + fR_bytes(c) * j;
+        }
+    }
+    w.fdEinv.alloc((size_t)MAX_ITERATED * MAX_ITERATED * sizeof(double2));
+    w.fdCoef.alloc((size_t)3 * MAX_ITERATED * sizeof(double2));
+    w.Gz.assign((size_t)k * k, cpx<double>());
+    w.Hz.assign((size_t)k * k, cpx<double>());
+    w.fd_k = k;
+    fdefl_all(c, M);
+}
+
+static void fdefl_end(Ctx &c) {
+    Ctx::Work &w = *c.work;
+    w.fd_k = 0;
+    w.QZ64all.free(); w.ZRall.free(); w.QZRall.free(); w.fdEinv.free(); w.fdCoef.free();
+    w.QZ64.clear(); w.fdZ.clear(); w.fdQZ.clear();
+}
+
+// E^-1 = (Z^dag Q Z - sigma Z^dag Z)^-1 for the next solve
+static void fdefl_prepare(Ctx &c, double sigma) {
+    Ctx::Work &w = *c.work;
+    const int k = w.fd_k;
+    if (!k) return;
+    std::vector<cpx<double>> E((size_t)k * k), Ei;
+    for (size_t q = 0; q < E.size(); ++q) E[q] = w.Hz[q] - cpx<double>(sigma) * w.Gz[q];
+    MG_REQUIRE(invert(k, E, Ei), MGEIG_EBREAKDOWN);
+    MG_CUDA(cudaMemcpyAsync(w.fdEinv.p, Ei.data(), Ei.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+    sync(c);
+}
+
+// z = M r for the FP64 Arnoldi vector v (z in the level precision R): the
+// two-grid cycle, deflated by Z when the eigensolver has set it up
+template <typename R>
+static void precondition(Ctx &c, double sigma, const void *v64, void *z) {
+    Ctx::Work &w = *c.work;
+    const size_t n = c.fine_ncpx();
+    const int k = w.fd_k;
+    if (sizeof(R) == 4) convert_f64_to_f32(c, v64, w.rR.p, n);
+    else if (k) blas_copy<double>(c, v64, w.rR.p, n);
+    const void *r = (sizeof(R) == 4 || k) ? w.rR.p : v64;
+    if (k) {
+        cpx<double> *cf = w.fdCoef.as<cpx<double>>();
+        cpx<double> *d = cf + MAX_ITERATED, *sd = cf + 2 * MAX_ITERATED;
+        blas_multidot<R>(c, (const void *const *)w.fdZ.data(), k, w.rR.p, n, cf);          // Z^dag r
+        small_gemv(c, w.fdEinv.as<cpx<double>>(), k, cf, -sigma, d, sd);                   // d, -sigma d
+        blas_multi_axpy<R>(c, w.rR.p, (const void *const *)w.fdQZ.data(), k, d, -1.0, n);  // r -= Q Z d
+        blas_multi_axpy<R>(c, w.rR.p, (const void *const *)w.fdZ.data(), k, sd, -1.0, n);  // r += sigma Z d
+    }
+    mg_cycle<R>(c, sigma, r, z);
+    if (k) blas_multi_axpy<R>(c, z, (const void *const *)w.fdZ.data(), k, w.fdCoef.as<cpx<double>>() + MAX_ITERATED, 1.0, n);
+}
+
+// ---------------------------------------------------------------------------
 // FGMRES (FP64) with the two-grid preconditioner
 
 template <typename R>
@@ -658,14 +776,9 @@ static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol,
         double est = beta;
         for (int j = 0; j < mm; ++j) {
             void *zj = w.Z[j].p;
-            if (sizeof(R) == 4) {
-                convert_f64_to_f32(c, V[j], w.rR.p, n);
-                mg_cycle<R>(c, sigma, w.rR.p, zj);
-                apply_fine_f64_from_f32(c, MODE_QSIGMA, sigma, zj, V[j + 1]);
-            } else {
-                mg_cycle<R>(c, sigma, V[j], zj);
-                apply_fine<double>(c, MODE_QSIGMA, sigma, zj, V[j + 1]);
-            }
+            precondition<R>(c, sigma, V[j], zj);
+            if (sizeof(R) == 4) apply_fine_f64_from_f32(c, MODE_QSIGMA, sigma, zj, V[j + 1]);
+            else apply_fine<double>(c, MODE_QSIGMA, sigma, zj, V[j + 1]);
             const double nrm = arnoldi_step<double>(c, V, j, V[j + 1], n, H);
             est = H.add_column(j);
             k = j + 1;
@@ -827,6 +940,8 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
     w.Psrc.assign(M.begin(), M.begin() + ntv);
     mg_rebuild(c);
     std::vector<double> lam(n_eig, 0.0), eps(n_eig, 1.0);
+    fdefl_begin(c, M, n_eig);
+    struct FdEnd { Ctx &c; ~FdEnd() { fdefl_end(c); } } fd_end{c};
     int sweeps = 0;
     const bool rr = c.prm.ritz_each_sweep != 0;
     // with the per-sweep Rayleigh-Ritz step converged pairs are locked, the
@@ -855,6 +970,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             const double dls = std::fabs(lam[i] - sigma);
             const double tau = (is_guard || dls == 0) ? c.prm.solve_tol
                                                       : std::min(c.prm.solve_tol, std::max(0.1 * tol / dls, 1e-12));
+            fdefl_prepare(c, sigma);
             int rc = fgmres_solve(c, sigma, M[i], w.x64.p, tau,
                                   is_guard ? std::min(c.prm.guard_maxiter, c.prm.outer_maxiter) : c.prm.outer_maxiter);
             if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
@@ -875,6 +991,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             blas_scale<double>(c, cpx<double>(1.0 / nrm), w.x64.p, N);
             blas_copy<double>(c, w.x64.p, M[i], N);
             if (i < ntv) mg_rebuild(c);   // P holds the first N_tv iterated vectors
+            if (w.fd_k) fdefl_update(c, M, i);
             auto le = rayleigh(c, M[i]);
             lam[i] = le.first;
             eps[i] = le.second;
@@ -887,22 +1004,28 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             }
         }
         if (rr) {
-            // lock the converged pairs; Rayleigh-Ritz on the others, orthogonal to them
+            // lock the converged pairs; the nearly converged ones (eps <= ritz_keep)
+            // are only orthonormalised, Rayleigh-Ritz on the others, orthogonal to both
             std::vector<void *> order;
-            std::vector<int> U;
+            std::vector<int> K, U;
             for (int i = 0; i < n_eig; ++i)
                 if (eps[i] <= tol) order.push_back(M[i]);
+                else if (eps[i] <= c.prm.ritz_keep) K.push_back(i);
                 else U.push_back(i);
-            const int nl = (int)order.size();
-            if (!U.empty()) {
+            const int nl = (int)order.size(), nk = (int)K.size();
+            if (!K.empty() || !U.empty()) {
+                for (int i : K) order.push_back(M[i]);
                 for (int i : U) order.push_back(M[i]);
                 orthonormalise_from(c, order, nl);
-                std::vector<void *> Mu(order.begin() + nl, order.end());
-                ritz_rotate(c, Mu, (int)Mu.size());
-                for (size_t k = 0; k < U.size(); ++k) {
-                    auto le = rayleigh(c, M[U[k]]);
-                    lam[U[k]] = le.first;
-                    eps[U[k]] = le.second;
+                if (!U.empty()) {
+                    std::vector<void *> Mu(order.begin() + nl + nk, order.end());
+                    ritz_rotate(c, Mu, (int)Mu.size());
+                }
+                for (int i : K) U.push_back(i);
+                for (int i : U) {
+                    auto le = rayleigh(c, M[i]);
+                    lam[i] = le.first;
+                    eps[i] = le.second;
                 }
             }
             // keep every vector in |lambda| order (a permutation of the pointers)
@@ -918,6 +1041,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             for (int k = 0; k < n_eig; ++k) { M[k] = M2[k]; lam[k] = l2[k]; eps[k] = e2[k]; }
             w.Psrc.assign(M.begin(), M.begin() + ntv);
             mg_rebuild(c);
+            fdefl_all(c, M);
             if (log_on()) {
                 double mx = 0;
                 for (int i = 0; i < n_want; ++i) mx = std::max(mx, eps[i]);
