@@ -127,6 +127,7 @@ typedef struct mgeig_stats {
     long long coarse_iters;   /* coarse GMRES iterations                        */
     long long fine_applies;   /* fine stencil applications (both precisions)    */
     double seconds;       /* wall time of the call                              */
+    long long kernel_launches;   /* CUDA kernels the call launched             */
 } mgeig_stats;
 
 /* Fill p with the library defaults (m0 = 0, c_sw = 1, periodic, 4^4 aggregates,
@@ -260,6 +261,11 @@ int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms,
  * its kernels, for callers that record CUDA events around device-pointer calls
  * such as mgeig_apply_dev.  Owned by the context. */
 int mgeig_get_stream(mgeig_ctx *ctx, void **stream);
+
+/* Number of CUDA kernels this context has launched since it was created (all
+ * calls, including mgeig_load_gauge*); *count is written on success.  The
+ * paper has no counterpart: it lets a caller count the device work of a step. */
+int mgeig_get_launch_count(mgeig_ctx *ctx, long long *count);
 
 /* Name of a status code. */
 const char *mgeig_strerror(int status);

@@ -40,6 +40,7 @@ class Stats(C.Structure):
     _fields_ = [
         ("sweeps", C.c_int), ("solves", C.c_int), ("outer_iters", C.c_int), ("mg_cycles", C.c_int),
         ("coarse_iters", C.c_longlong), ("fine_applies", C.c_longlong), ("seconds", C.c_double),
+        ("kernel_launches", C.c_longlong),
     ]
 
     def as_dict(self):
@@ -92,6 +93,7 @@ def load():
         "mgeig_set_timing": (I, [P, I]),
         "mgeig_kernel_times": (I, [P, I, P, P, P, P]),
         "mgeig_get_stream": (I, [P, C.POINTER(P)]),
+        "mgeig_get_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
         "mgeig_strerror": (C.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -290,6 +292,11 @@ class Context:
         s = C.c_void_p()
         self._check("mgeig_get_stream", self.lib.mgeig_get_stream(self._h, C.byref(s)))
         return s.value or 0
+
+    def launch_count(self) -> int:
+        n = C.c_longlong()
+        self._check("mgeig_get_launch_count", self.lib.mgeig_get_launch_count(self._h, C.byref(n)))
+        return int(n.value)
 
     def set_timing(self, on: bool):
         self._check("mgeig_set_timing", self.lib.mgeig_set_timing(self._h, 1 if on else 0))

@@ -333,9 +333,13 @@ static int need_setup(Ctx &c) {
     return MGEIG_OK;
 }
 
-static void begin_stats(Ctx &c) { std::memset(&c.st, 0, sizeof(c.st)); }
+static void begin_stats(Ctx &c) {
+    std::memset(&c.st, 0, sizeof(c.st));
+    c.st.kernel_launches = -c.launches;
+}
 static void end_stats(Ctx &c, mgeig_stats *out, std::chrono::steady_clock::time_point t0) {
     coarse_iters_take(c);
+    c.st.kernel_launches += c.launches;
     c.st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (out) *out = c.st;
 }
@@ -537,6 +541,12 @@ int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms, d
 int mgeig_get_stream(mgeig_ctx *ctx, void **stream) {
     if (!ctx || !stream) return MGEIG_EINVAL;
     *stream = (void *)ctx->c.stream;
+    return MGEIG_OK;
+}
+
+int mgeig_get_launch_count(mgeig_ctx *ctx, long long *count) {
+    if (!ctx || !count) return MGEIG_EINVAL;
+    *count = ctx->c.launches;
     return MGEIG_OK;
 }
 

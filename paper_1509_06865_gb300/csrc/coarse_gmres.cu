@@ -558,6 +558,7 @@ void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, con
     void *args[] = {&a};
     TimeScope ts(c.timer, K_COARSE_SOLVE, 0);
     MG_CUDA(cudaLaunchCooperativeKernel((void *)coarse_gmres_kernel<R>, dim3(G), dim3(CG_THREADS), args, 0, c.stream));
+    ++c.launches;
 }
 
 template void coarse_gmres_persistent<float>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);

@@ -29,7 +29,13 @@ struct Error {
         }                                                                                  \
     } while (0)
 
-#define MG_CHECK_LAUNCH() MG_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by this check, which also
+// counts it on the context `c` in scope
+#define MG_CHECK_LAUNCH()                \
+    do {                                 \
+        MG_CUDA(cudaGetLastError());     \
+        ++c.launches;                    \
+    } while (0)
 
 #define MG_REQUIRE(cond, code)           \
     do {                                 \
@@ -180,6 +186,7 @@ struct Ctx {
 
     // host workspace counters
     mgeig_stats st{};
+    long long launches = 0;   // kernel launches since the context was created
 
     // solver workspace (allocated lazily, see solver.cu)
     struct Work;

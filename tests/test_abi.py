@@ -58,3 +58,12 @@ def test_params_struct_matches_header():
     names = [f for f, _ in Params._fields_]
     order = [n for n in re.findall(r"([a-z0-9_]+)(?:\[4\])?\s*[;,]", body)]
     assert order == names
+
+
+def test_stats_struct_matches_header():
+    from paper_1509_06865_gb300._lib import Stats
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct mgeig_stats \{(.*?)\} mgeig_stats;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    order = re.findall(r"([a-z0-9_]+)\s*;", body)
+    assert order == [f for f, _ in Stats._fields_]
