@@ -51,6 +51,8 @@ extern "C" {
 #define MGEIG_EBREAKDOWN (-5)  /* NaN/Inf or a zero Krylov vector where none may appear */
 #define MGEIG_ENOMEM (-6)      /* device allocation failed                              */
 #define MGEIG_ETIMEOUT (-7)    /* a bounded device-side wait expired (grid barrier)     */
+#define MGEIG_ESCRATCH (-8)    /* coarse grid too large for the static scratch of
+                                  mgeig_mg_cycle_dev_noalloc                            */
 
 /* precision of the multigrid preconditioner (Sec. 2.2: double precision FGMRES
  * around a single precision multigrid method) */
@@ -225,6 +227,29 @@ int mgeig_sap(mgeig_ctx *ctx, double sigma, const double *b, double *z, int cycl
  * with no pre- and nu post-smoothing steps): coarse GMRES on Q_c - sigma (tol,
  * coarse_maxiter), prolongation, then the smoother.  Host spinors. */
 int mgeig_mg_cycle(mgeig_ctx *ctx, double sigma, const double *r, double *z);
+
+/* The same two-grid application z = B r, for callers that cannot allocate
+ * device memory while they run (a framework whose pool allocator holds all free
+ * GPU memory, a latency-bound loop that must not take the driver's allocation
+ * lock or let cudaFree synchronise the device).  The paper has no counterpart.
+ *   r, z   device spinors in the context's level precision and internal layout
+ *          (MGEIG_PREC_F32 for MGEIG_MIXED, MGEIG_PREC_F64 for MGEIG_FP64, as
+ *          mgeig_pack_spinors writes them); r is read, z is overwritten.  The
+ *          caller owns both.
+ * The result equals mgeig_mg_cycle's.  On success the call allocates nothing:
+ * the coarse vectors and the coarse solver's scratch live in one static device
+ * array of 16 MiB that every GPU loading this library holds until the process
+ * exits.  Coarse grids needing more (about (coarse_restart + 4) x n_agg x
+ * 2 n_tv complex values in the level precision, plus the solver's per-block
+ * partial sums) return MGEIG_ESCRATCH; the 16^3 x 32 lattice with 4^4
+ * aggregates and 20 test vectors fits in both precisions.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU race.  Needs the SAP smoother and kernel timing off
+ * (MGEIG_EINVAL otherwise); the coarse-grid deflation data for sigma is
+ * computed on the first call at a new sigma, as in mgeig_mg_cycle.  Returns
+ * after the cycle has finished on the context's stream. */
+int mgeig_mg_cycle_dev_noalloc(mgeig_ctx *ctx, double sigma, const void *r, void *z);
 
 /* Solve (Q - sigma) x = b with FP64 flexible GMRES preconditioned by the two-grid
  * method (Sec. 2.2) to relative residual tol.  ENOCONV if outer_maxiter is hit. */

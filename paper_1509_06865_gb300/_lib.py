@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmgeig.so")
 
-OK, EINVAL, ENOTSETUP, ECUDA, ENOCONV, EBREAKDOWN, ENOMEM, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOTSETUP, ECUDA, ENOCONV, EBREAKDOWN, ENOMEM, ETIMEOUT, ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FP64, MIXED = 0, 1
 SAP, GMRES = 0, 1
 OP_Q, OP_D = 0, 1
@@ -94,6 +94,7 @@ def load():
         "mgeig_kernel_times": (I, [P, I, P, P, P, P]),
         "mgeig_get_stream": (I, [P, C.POINTER(P)]),
         "mgeig_get_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
+        "mgeig_mg_cycle_dev_noalloc": (I, [P, D, P, P]),
         "mgeig_strerror": (C.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -267,6 +268,13 @@ class Context:
         z = np.empty_like(r)
         self._check("mgeig_mg_cycle", self.lib.mgeig_mg_cycle(self._h, float(sigma), _ptr(r), _ptr(z)))
         return z
+
+    def mg_cycle_dev_noalloc(self, r_dev: int, z_dev: int, sigma=0.0):
+        """z = B r on device spinors of the level precision (see the C header):
+        for callers that cannot allocate device memory during the call; the
+        scratch is a static 16 MiB device array shared by all calls."""
+        self._check("mgeig_mg_cycle_dev_noalloc",
+                    self.lib.mgeig_mg_cycle_dev_noalloc(self._h, float(sigma), C.c_void_p(r_dev), C.c_void_p(z_dev)))
 
     def solve(self, b, sigma=0.0, tol=1e-10):
         b = _c128(b)

@@ -482,6 +482,15 @@ int mgeig_mg_cycle(mgeig_ctx *ctx, double sigma, const double *r, double *z) {
     });
 }
 
+int mgeig_mg_cycle_dev_noalloc(mgeig_ctx *ctx, double sigma, const void *r, void *z) {
+    if (!r || !z || !std::isfinite(sigma)) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        if (c.prm.smoother != MGEIG_SAP || c.timer.on) return MGEIG_EINVAL;
+        return mg_cycle_noalloc(c, sigma, r, z);
+    });
+}
+
 int mgeig_solve(mgeig_ctx *ctx, double sigma, const double *b, double *x, double tol, mgeig_stats *stats) {
     if (!b || !x || !(tol > 0)) return MGEIG_EINVAL;
     return guarded(ctx, [&](Ctx &c) {
@@ -560,6 +569,7 @@ const char *mgeig_strerror(int status) {
         case MGEIG_EBREAKDOWN: return "numerical breakdown (NaN/Inf or zero vector)";
         case MGEIG_ENOMEM: return "device memory allocation failed";
         case MGEIG_ETIMEOUT: return "a bounded device-side wait expired";
+        case MGEIG_ESCRATCH: return "coarse grid too large for the static scratch of mgeig_mg_cycle_dev_noalloc";
         default: return "unknown status";
     }
 }

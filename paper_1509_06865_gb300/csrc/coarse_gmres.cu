@@ -564,4 +564,63 @@ void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, con
 template void coarse_gmres_persistent<float>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);
 template void coarse_gmres_persistent<double>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);
 
+// The same persistent coarse solve, with its scratch at caller-given device
+// addresses instead of context buffers: the Krylov basis V ((m + 1) n level
+// complex values), the projected right-hand side rhs (n), the per-block
+// partial sums (coarse_gmres_partial_bytes) and the CGState word block
+// (16 bytes, zero on entry).  Grid size and restart length are those of
+// coarse_gmres_persistent, so both give the same result.
+int coarse_gmres_grid(Ctx &c) {
+    const int n = c.nagg * 2 * c.prm.n_tv;
+    int dev_sms = 0;
+    MG_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device));
+    int per_sm = 0;
+    if (c.mixed())
+        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel<float>, CG_THREADS, 0));
+    else
+        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel<double>, CG_THREADS, 0));
+    MG_REQUIRE(per_sm >= 1, MGEIG_ECUDA);
+    int G = (n * TPR + CG_THREADS - 1) / CG_THREADS;
+    return std::max(1, std::min(G, std::min(dev_sms * per_sm, dev_sms)));
+}
+
+size_t coarse_gmres_partial_bytes(Ctx &c, int G) {
+    return (size_t)G * CG_SLOTS * (c.mixed() ? sizeof(float2) : sizeof(double2));
+}
+
+template <typename R>
+void coarse_gmres_at(Ctx &c, int G, double sigma, const void *rc, void *ec, void *V, void *rhs, void *partial,
+                     void *state, int k, const void *W, const void *AW, const void *Einv) {
+    const int ntv = c.prm.n_tv;
+    MG_REQUIRE(k <= CG_MAXK, MGEIG_EINVAL);
+    CGArgs<R> a;
+    a.nagg = c.nagg; a.ntv = ntv; a.n = c.nagg * 2 * ntv;
+    for (int mu = 0; mu < 4; ++mu) a.cd[mu] = c.cdims[mu];
+    a.Dc = static_cast<const cpx<R> *>(c.Dc.p);
+    a.sigma = (R)sigma;
+    a.b = static_cast<const cpx<R> *>(rc);
+    a.x = static_cast<cpx<R> *>(ec);
+    a.rhs = static_cast<cpx<R> *>(rhs);
+    a.V = static_cast<cpx<R> *>(V);
+    a.k = k;
+    a.W = static_cast<const cpx<R> *>(W);
+    a.AW = static_cast<const cpx<R> *>(AW);
+    a.Einv = static_cast<const double2 *>(Einv);
+    a.partial = static_cast<typename Pod2<R>::T *>(partial);
+    a.st = static_cast<CGState *>(state);
+    a.m = std::min(c.prm.coarse_restart, CG_MAXM);
+    a.maxiter = c.prm.coarse_maxiter;
+    a.tol = c.prm.coarse_tol;
+    a.timeout = 4000000000LL;   // about 2 s of SM clock per barrier wait
+    void *args[] = {&a};
+    TimeScope ts(c.timer, K_COARSE_SOLVE, 0);
+    MG_CUDA(cudaLaunchCooperativeKernel((void *)coarse_gmres_kernel<R>, dim3(G), dim3(CG_THREADS), args, 0, c.stream));
+    ++c.launches;
+}
+
+template void coarse_gmres_at<float>(Ctx &, int, double, const void *, void *, void *, void *, void *, void *, int,
+                                     const void *, const void *, const void *);
+template void coarse_gmres_at<double>(Ctx &, int, double, const void *, void *, void *, void *, void *, void *, int,
+                                      const void *, const void *, const void *);
+
 }  // namespace mgeig

@@ -144,6 +144,12 @@ struct CoarseSolveBufs {
 };
 template <typename R>
 void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, const void *rc, void *ec);
+// the same solve with caller-placed scratch (coarse_gmres.cu)
+int coarse_gmres_grid(Ctx &c);
+size_t coarse_gmres_partial_bytes(Ctx &c, int G);
+template <typename R>
+void coarse_gmres_at(Ctx &c, int G, double sigma, const void *rc, void *ec, void *V, void *rhs, void *partial,
+                     void *state, int k, const void *W, const void *AW, const void *Einv);
 
 // ----- the context -----
 struct Ctx {
@@ -206,6 +212,9 @@ void *mg_test_vector(Ctx &c, int j);
 void mg_rebuild(Ctx &c);   // P and coarse operator from c.W
 void setup(Ctx &c, uint64_t seed);
 void mg_cycle_host(Ctx &c, double sigma, const double *r_dev64_internal, double *z_dev64_internal);
+// the two-grid cycle on level-precision device spinors, scratch in a static device array
+int mg_cycle_noalloc(Ctx &c, double sigma, const void *r, void *z);
+size_t mg_cycle_noalloc_limit();
 int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol, int maxiter = 0);
 int eigensolve(Ctx &c, int n_eig, double tol, double *evals, double *evecs_host, double *resid);
 void sap_smooth_f64(Ctx &c, double sigma, const void *b64, void *z64, int cycles);

@@ -15,6 +15,8 @@
 
 #include <cstdlib>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace mgeig {
@@ -1210,6 +1212,157 @@ void interp_f64(Ctx &c, void *const *out64) {
         if (c.mixed()) convert_f32_to_f64(c, w.P[j], out64[j], c.fine_ncpx());
         else MG_CUDA(cudaMemcpyAsync(out64[j], w.P64[j], f64_bytes(c), cudaMemcpyDeviceToDevice, c.stream));
     }
+}
+
+// ---------------------------------------------------------------------------
+// The two-grid cycle without device allocation (mgeig_mg_cycle_dev_noalloc).
+//
+// Some callers cannot allocate device memory when they need a preconditioner
+// application: a solver embedded in a framework whose pool allocator owns all
+// free GPU memory, a latency-critical loop that must not take the driver's
+// allocation lock or let cudaFree synchronise the device, or a host thread
+// that runs while another library holds the GPU to a fixed memory budget.
+// For them the cycle's coarse vectors and the persistent coarse solver's
+// scratch (Krylov basis, projected right-hand side, per-block partial sums,
+// barrier and status words) live in one file-scope device array of
+// NOALLOC_SCRATCH_BYTES; every GPU that loads this library holds it until
+// the process exits.  All calls share it, so calls that overlap on the GPU
+// (other streams, other contexts on the same device, other host threads) race.
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+size_t mg_cycle_noalloc_limit() { return NOALLOC_SCRATCH_BYTES; }
+
+// Device address of noalloc_scratch on `device` (which must be current): in host
+// code the array's name only stands in for the symbol, so the address is looked
+// up with cudaGetSymbolAddress once per device and cached.
+static void *noalloc_scratch_address(int device) {
+    constexpr int MAX_DEVICES = 64;
+    static std::mutex mu;
+    static void *addr[MAX_DEVICES] = {};
+    MG_REQUIRE(device >= 0 && device < MAX_DEVICES, MGEIG_EINVAL);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        MG_CUDA(cudaGetSymbolAddress(&p, noalloc_scratch));
+        addr[device] = p;
+    }
+    return addr[device];
+}
+
+// Gauss-Jordan inverse of the row-major n x n matrix A (destroyed), n <= 24,
+// with the operations of invert() in the same order (identical results) but
+// on the caller's arrays.
+static bool invert_fixed(int n, cpx<double> *A, cpx<double> *inv) {
+    for (int i = 0; i < n * n; ++i) inv[i] = cpx<double>();
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = cpx<double>(1);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        double best = -1;
+        for (int r = col; r < n; ++r) {
+            cpx<double> z = A[(size_t)r * n + col];
+            double m = std::hypot(z.re, z.im);
+            if (m > best) { best = m; piv = r; }
+        }
+        if (!(best > 0) || !std::isfinite(best)) return false;
+        if (piv != col)
+            for (int k = 0; k < n; ++k) {
+                std::swap(A[(size_t)piv * n + k], A[(size_t)col * n + k]);
+                std::swap(inv[(size_t)piv * n + k], inv[(size_t)col * n + k]);
+            }
+        cpx<double> d = A[(size_t)col * n + col];
+        double dd = d.re * d.re + d.im * d.im;
+        cpx<double> di(d.re / dd, -d.im / dd);
+        for (int k = 0; k < n; ++k) {
+            A[(size_t)col * n + k] = A[(size_t)col * n + k] * di;
+            inv[(size_t)col * n + k] = inv[(size_t)col * n + k] * di;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            cpx<double> f = A[(size_t)r * n + col];
+            if (f.re == 0 && f.im == 0) continue;
+            for (int k = 0; k < n; ++k) {
+                A[(size_t)r * n + k] = A[(size_t)r * n + k] - f * A[(size_t)col * n + k];
+                inv[(size_t)r * n + k] = inv[(size_t)r * n + k] - f * inv[(size_t)col * n + k];
+            }
+        }
+    }
+    return true;
+}
+
+// deflation_prepare with host arrays on the stack instead of the heap
+template <typename R>
+static void deflation_prepare_fixed(Ctx &c, double sigma) {
+    Ctx::Work &w = *c.work;
+    if (w.defl_valid && w.defl_sigma == sigma) return;
+    constexpr int KMAX = 24;
+    const int k = c.prm.n_tv;
+    MG_REQUIRE(k <= KMAX, MGEIG_EINVAL);
+    const size_t n = c.coarse_ncpx(), vb = cR_bytes(c);
+    const void *Wp[KMAX];
+    for (int i = 0; i < k; ++i) Wp[i] = static_cast<const char *>(w.Wc.p) + vb * i;
+    for (int j = 0; j < k; ++j) {
+        void *awj = static_cast<char *>(w.AWc.p) + vb * j;
+        coarse_apply<R>(c, c.Dc.p, sigma, Wp[j], awj, false);
+        blas_multidot<R>(c, Wp, k, awj, n, w.Edev.as<cpx<double>>() + (size_t)j * k);
+    }
+    cpx<double> Ecol[KMAX * KMAX], E[KMAX * KMAX], Ei[KMAX * KMAX];
+    MG_CUDA(cudaMemcpyAsync(Ecol, w.Edev.p, (size_t)k * k * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) E[(size_t)i * k + j] = Ecol[(size_t)j * k + i];   // E_ij = <W_i, A W_j>
+    MG_REQUIRE(invert_fixed(k, E, Ei), MGEIG_EBREAKDOWN);
+    MG_CUDA(cudaMemcpyAsync(w.Einv.p, Ei, (size_t)k * k * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+    sync(c);
+    w.defl_valid = true;
+    w.defl_sigma = sigma;
+}
+
+template <typename R>
+static int mg_cycle_noalloc_impl(Ctx &c, double sigma, const void *r, void *z) {
+    Ctx::Work &w = *c.work;
+    const size_t cb = c.coarse_ncpx() * sizeof(cpx<R>);
+    const int m = std::min(c.prm.coarse_restart, COARSE_PERSISTENT_MAXM);
+    const int G = coarse_gmres_grid(c);
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    // layout: solver state words | r_c | e_c | projected rhs | basis | partial sums
+    const size_t off_rc = 256, off_ec = off_rc + up(cb), off_rhs = off_ec + up(cb), off_V = off_rhs + up(cb);
+    const size_t off_P = off_V + up((size_t)(m + 1) * cb);
+    const size_t need = off_P + up(coarse_gmres_partial_bytes(c, G));
+    if (need > NOALLOC_SCRATCH_BYTES) {
+        fprintf(stderr, "libmgeig: mgeig_mg_cycle_dev_noalloc needs %zu bytes of scratch for this coarse grid, "
+                        "its static array holds %zu\n", need, NOALLOC_SCRATCH_BYTES);
+        return MGEIG_ESCRATCH;
+    }
+    char *s = static_cast<char *>(noalloc_scratch_address(c.device));
+    // the barrier counters, status and iteration words must start at zero
+    MG_CUDA(cudaMemsetAsync(s, 0, 256, c.stream));
+    int k = 0;
+    if (c.prm.coarse_deflate) {
+        deflation_prepare_fixed<R>(c, sigma);
+        k = c.prm.n_tv;
+    }
+    c.st.mg_cycles += 1;
+    restrict_vec<R>(c, (const void *const *)w.P.data(), r, s + off_rc);
+    coarse_gmres_at<R>(c, G, sigma, s + off_rc, s + off_ec, s + off_V, s + off_rhs, s + off_P, s, k, w.Wc.p, w.AWc.p,
+                       w.Einv.p);
+    prolong_vec<R>(c, (const void *const *)w.P.data(), s + off_ec, z);
+    for (int q = 0; q < c.prm.sap_cycles; ++q) {
+        sap_sweep<R>(c, 0, sigma, r, true, z);
+        sap_sweep<R>(c, 1, sigma, r, true, z);
+    }
+    int state[4];   // barrier count, generation, status (0 ok, 1 timeout, 2 breakdown), iterations
+    MG_CUDA(cudaMemcpyAsync(state, s, sizeof(state), cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+    c.st.coarse_iters += state[3];
+    if (state[2] == 1) return MGEIG_ETIMEOUT;
+    if (state[2] != 0) return MGEIG_EBREAKDOWN;
+    return MGEIG_OK;
+}
+
+int mg_cycle_noalloc(Ctx &c, double sigma, const void *r, void *z) {
+    return c.mixed() ? mg_cycle_noalloc_impl<float>(c, sigma, r, z) : mg_cycle_noalloc_impl<double>(c, sigma, r, z);
 }
 
 }  // namespace mgeig
