@@ -118,6 +118,9 @@ typedef struct mgeig_params {
                              the preconditioner becomes
                              z = Z E^-1 Z^dag r + B (r - (Q - sigma) Z E^-1 Z^dag r),
                              E = Z^dag (Q - sigma) Z formed in FP64; 0: plain B */
+    double fine_deflate_radius;  /* Z of the solve for v_i: v_i and the iterated
+                             vectors whose Rayleigh quotient lies within this
+                             distance of sigma (< 0: all iterated vectors)      */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */

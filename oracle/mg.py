@@ -356,13 +356,14 @@ DEFAULT_PARAMS = dict(
     gmres_smooth_k=8,
     coarse_tol=5e-2,
     coarse_restart=30,
-    coarse_maxiter=64,
+    coarse_maxiter=24,
     coarse_deflate=True,
     ritz_each_sweep=True,
     shift_floor=1e-6,
     guard_maxiter=8,
     ritz_keep=1e-6,
     fine_deflate=True,
+    fine_deflate_radius=-1.0,
     outer_restart=20,
     outer_maxiter=50,
     solve_tol=1e-2,

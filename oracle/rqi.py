@@ -24,8 +24,9 @@ Algorithm 1, per sweep over the unconverged i:
     v_i    <- (Q - sigma)^-1 v_i                           (FGMRES + two-grid, FP64, to
               relative residual min(solve_tol, 0.1 eps / |lambda_i - sigma|): the
               new vector's eigen-residual is about that tolerance times |lambda_i - sigma|;
-              with fine_deflate the two-grid preconditioner is deflated by all
-              iterated vectors, see deflated_preconditioner)
+              with fine_deflate the two-grid preconditioner is deflated by v_i and
+              the iterated vectors whose Rayleigh quotient lies within
+              fine_deflate_radius of sigma, see deflated_preconditioner)
     v_i    <- v_i - sum_{j<i} <v_j|v_i> v_j                 (classical GS, done twice)
     v_i    <- v_i / ||v_i||
     update v_i in P (rebuild P and the coarse operator)
@@ -161,8 +162,14 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
             # inexact solve: the new vector's eigen-residual is about tau |lambda - sigma|
             dls = abs(lam[i] - sigma)
             tau = p["solve_tol"] if (guard or dls == 0) else min(p["solve_tol"], max(0.1 * eps / dls, 1e-12))
-            precond = (lambda r: B(r, sigma)) if not p.get("fine_deflate", False) else \
-                deflated_preconditioner(op, np.array(V), B, sigma)
+            if p.get("fine_deflate", False):
+                # z_i and the iterated vectors with Rayleigh quotient within the radius of sigma
+                rad = p.get("fine_deflate_radius", -1.0)
+                theta = [np.real(np.vdot(v, op.Q(v))) / np.real(np.vdot(v, v)) for v in V]
+                S = [i] + [j for j in range(n_eig) if j != i and (rad < 0 or abs(theta[j] - sigma) <= rad)]
+                precond = deflated_preconditioner(op, np.array([V[j] for j in S]), B, sigma)
+            else:
+                precond = lambda r: B(r, sigma)
             x, info = krylov.fgmres(lambda v: op.Q_sigma(v, sigma), precond, V[i],
                                     tol=tau, restart=p["outer_restart"], maxiter=maxit)
             stats["solves"] += 1

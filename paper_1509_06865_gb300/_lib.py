@@ -32,7 +32,7 @@ class Params(C.Structure):
         ("solve_tol", C.c_double), ("precision", C.c_int), ("smoother", C.c_int), ("max_sweeps", C.c_int),
         ("n_guard", C.c_int), ("coarse_deflate", C.c_int), ("ritz_each_sweep", C.c_int),
         ("shift_floor", C.c_double), ("guard_maxiter", C.c_int), ("ritz_keep", C.c_double),
-        ("fine_deflate", C.c_int),
+        ("fine_deflate", C.c_int), ("fine_deflate_radius", C.c_double),
     ]
 
 

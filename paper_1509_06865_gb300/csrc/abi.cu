@@ -54,6 +54,7 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (!(p.shift_floor >= 0 && p.shift_floor < 1) || p.guard_maxiter < 1) return MGEIG_EINVAL;
     if (!(p.ritz_keep >= 0) || !std::isfinite(p.ritz_keep)) return MGEIG_EINVAL;
     if (p.fine_deflate != 0 && p.fine_deflate != 1) return MGEIG_EINVAL;
+    if (!std::isfinite(p.fine_deflate_radius)) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES) return MGEIG_EINVAL;
@@ -95,7 +96,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->outer_restart = 20;
     p->outer_maxiter = 50;
     p->coarse_restart = 30;
-    p->coarse_maxiter = 64;
+    p->coarse_maxiter = 24;
     p->coarse_tol = 5e-2;
     p->solve_tol = 1e-2;
     p->precision = MGEIG_MIXED;
@@ -108,6 +109,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->guard_maxiter = 8;
     p->ritz_keep = 1e-6;
     p->fine_deflate = 1;
+    p->fine_deflate_radius = -1.0;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {

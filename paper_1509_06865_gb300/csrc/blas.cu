@@ -5,7 +5,7 @@
 // blocks accumulates grid-stride partial sums (per thread in the array's own
 // precision, then in FP64 across the block with warp shuffles), writes one
 // partial per block, and a second kernel adds the partials in a fixed order.
-// Inner products of up to 8 vectors against one vector share one read of that
+// Inner products of up to 16 vectors against one vector share one read of that
 // vector (the Arnoldi / Gram-Schmidt steps of GMRES, FGMRES and Algorithm 1).
 #include "internal.h"
 
@@ -13,7 +13,10 @@ namespace mgeig {
 
 constexpr int RED_THREADS = 256;
 constexpr int RED_MAXBLOCKS = 1024;
-constexpr int CHUNK = 8;
+constexpr int CHUNK = 16;   // pointer slots per launch
+// vectors per launch: 16 in FP32 (bandwidth bound, fewer passes over y); 8 in
+// FP64, where the FP64 pipe bounds the kernel and 16 accumulators cost occupancy
+template <typename R> struct Chunk { static constexpr int n = sizeof(R) == 4 ? 16 : 8; };
 
 template <typename R> struct V2;
 template <> struct V2<double> { typedef double2 T; };
@@ -60,13 +63,14 @@ __global__ void __launch_bounds__(RED_THREADS) multidot_kernel(PtrPack X, int k,
                                                                double2 *__restrict__ partial, size_t pstride) {
     typedef typename V2<R>::T T;
     const T *y = static_cast<const T *>(yv);
-    R ar[CHUNK], ai[CHUNK];
+    constexpr int C = Chunk<R>::n;
+    R ar[C], ai[C];
 #pragma unroll
-    for (int j = 0; j < CHUNK; ++j) { ar[j] = 0; ai[j] = 0; }
+    for (int j = 0; j < C; ++j) { ar[j] = 0; ai[j] = 0; }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         T b = y[i];
 #pragma unroll
-        for (int j = 0; j < CHUNK; ++j) {
+        for (int j = 0; j < C; ++j) {
             if (j < k) {
                 T a = static_cast<const T *>(X.p[j])[i];
                 ar[j] = fma(a.x, b.x, ar[j]); ar[j] = fma(a.y, b.y, ar[j]);
@@ -74,10 +78,10 @@ __global__ void __launch_bounds__(RED_THREADS) multidot_kernel(PtrPack X, int k,
             }
         }
     }
-    double re[CHUNK], im[CHUNK];
+    double re[C], im[C];
 #pragma unroll
-    for (int j = 0; j < CHUNK; ++j) { re[j] = ar[j]; im[j] = ai[j]; }
-    block_reduce_store<CHUNK>(re, im, k, partial, pstride);
+    for (int j = 0; j < C; ++j) { re[j] = ar[j]; im[j] = ai[j]; }
+    block_reduce_store<C>(re, im, k, partial, pstride);
 }
 
 template <typename R>
@@ -131,9 +135,10 @@ void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n,
     const int nb = red_grid(n);
     const size_t pstride = RED_MAXBLOCKS;
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)(k + 1) * n * 2 * sizeof(R));
-    for (int j0 = 0; j0 < k; j0 += CHUNK) {
+    constexpr int C = Chunk<R>::n;
+    for (int j0 = 0; j0 < k; j0 += C) {
         PtrPack pk{};
-        const int kk = k - j0 < CHUNK ? k - j0 : CHUNK;
+        const int kk = k - j0 < C ? k - j0 : C;
         for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
         multidot_kernel<R><<<nb, RED_THREADS, 0, c.stream>>>(pk, kk, y, n, partial_ptr(c) + (size_t)j0 * pstride, pstride);
         MG_CHECK_LAUNCH();
@@ -168,16 +173,17 @@ __global__ void multi_axpy_kernel(void *__restrict__ yv, PtrPack X, int k, const
                                   size_t n) {
     typedef typename V2<R>::T T;
     T *y = static_cast<T *>(yv);
-    R cr[CHUNK], ci[CHUNK];
+    constexpr int C = Chunk<R>::n;
+    R cr[C], ci[C];
 #pragma unroll
-    for (int j = 0; j < CHUNK; ++j) {
+    for (int j = 0; j < C; ++j) {
         if (j < k) { double2 t = coef[j]; cr[j] = (R)(sign * t.x); ci[j] = (R)(sign * t.y); }
         else { cr[j] = 0; ci[j] = 0; }
     }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         T acc = y[i];
 #pragma unroll
-        for (int j = 0; j < CHUNK; ++j) {
+        for (int j = 0; j < C; ++j) {
             if (j < k) {
                 T a = static_cast<const T *>(X.p[j])[i];
                 acc.x = fma(cr[j], a.x, acc.x); acc.x = fma(-ci[j], a.y, acc.x);
@@ -197,9 +203,10 @@ static int ew_grid(size_t n) {
 template <typename R>
 void blas_multi_axpy(Ctx &c, void *y, const void *const *X, int k, const cpx<double> *d_coef, double sign, size_t n) {
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)(k + 2) * n * 2 * sizeof(R));
-    for (int j0 = 0; j0 < k; j0 += CHUNK) {
+    constexpr int C = Chunk<R>::n;
+    for (int j0 = 0; j0 < k; j0 += C) {
         PtrPack pk{};
-        const int kk = k - j0 < CHUNK ? k - j0 : CHUNK;
+        const int kk = k - j0 < C ? k - j0 : C;
         for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
         multi_axpy_kernel<R><<<ew_grid(n), 256, 0, c.stream>>>(y, pk, kk, reinterpret_cast<const double2 *>(d_coef + j0),
                                                                sign, n);

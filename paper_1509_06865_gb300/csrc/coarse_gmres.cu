@@ -58,6 +58,7 @@ struct CGArgs {
     int nagg, ntv, n;              // coarse sites, test vectors, rows = nagg * 2 ntv
     int cd[4];                     // coarse lattice extents
     const cpx<R> *Dc;              // [9][nagg][col][row]
+    const int *nbr;                // [9][nagg] neighbour aggregates
     R sigma;
     const cpx<R> *b;               // r_c
     cpx<R> *x;                     // e (output); holds y during the iteration
@@ -125,17 +126,9 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
         cpx<R> acc0, acc1;
         if (t < r1) {
             const int site = t / n2, row = t % n2;
-            int ac[4], rem = site;
-            for (int mu = 0; mu < 4; ++mu) { ac[mu] = rem % a.cd[mu]; rem /= a.cd[mu]; }
 #pragma unroll 3
             for (int d = 0; d < 9; ++d) {
-                int nb = site;
-                if (d > 0) {
-                    const int mu = (d - 1) / 2, step = (d & 1) ? 1 : -1;
-                    int bc[4] = {ac[0], ac[1], ac[2], ac[3]};
-                    bc[mu] = (bc[mu] + step + a.cd[mu]) % a.cd[mu];
-                    nb = ((bc[3] * a.cd[2] + bc[2]) * a.cd[1] + bc[1]) * a.cd[0] + bc[0];
-                }
+                const int nb = __ldg(a.nbr + (size_t)d * a.nagg + site);
                 const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
                 const cpx<R> *xb = v + (size_t)nb * n2;
                 int j = q;
@@ -539,6 +532,7 @@ void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, con
     a.nagg = c.nagg; a.ntv = ntv; a.n = n;
     for (int mu = 0; mu < 4; ++mu) a.cd[mu] = c.cdims[mu];
     a.Dc = static_cast<const cpx<R> *>(c.Dc.p);
+    a.nbr = c.cnbr.as<int>();
     a.sigma = (R)sigma;
     a.b = static_cast<const cpx<R> *>(rc);
     a.x = static_cast<cpx<R> *>(ec);
@@ -597,6 +591,7 @@ void coarse_gmres_at(Ctx &c, int G, double sigma, const void *rc, void *ec, void
     a.nagg = c.nagg; a.ntv = ntv; a.n = c.nagg * 2 * ntv;
     for (int mu = 0; mu < 4; ++mu) a.cd[mu] = c.cdims[mu];
     a.Dc = static_cast<const cpx<R> *>(c.Dc.p);
+    a.nbr = c.cnbr.as<int>();
     a.sigma = (R)sigma;
     a.b = static_cast<const cpx<R> *>(rc);
     a.x = static_cast<cpx<R> *>(ec);

@@ -184,6 +184,7 @@ struct Ctx {
     std::vector<DevBuf> W;    // ntv FP64 fine vectors
     std::vector<DevBuf> P;    // ntv vectors, R precision
     DevBuf Dc;                // [9][nagg][2N][2N] (column-major blocks), R precision
+    DevBuf cnbr;              // coarse neighbour table int32 [9][nagg]: self, then +mu, -mu for mu = 0..3
 
     size_t fine_ncpx() const { return (size_t)g.V * 12; }
     size_t coarse_ncpx() const { return (size_t)nagg * 2 * prm.n_tv; }

@@ -102,7 +102,7 @@ constexpr int H1 = 0, H2 = 128, HN = 256, CGS = 257, NFETCH = 258, UP = 300;
 void ensure_reduction(Ctx &c, int max_vectors) {
     (void)max_vectors;
     if (!c.red_partial.p) {
-        c.red_partial.alloc((size_t)64 * 1024 * sizeof(double2));
+        c.red_partial.alloc((size_t)(MAX_ITERATED + 8) * 1024 * sizeof(double2));   // >= (vectors + 1) x 1024 blocks
         c.red_out.alloc(RED_SLOTS * sizeof(double2));
         MG_CUDA(cudaMemset(c.red_out.p, 0, RED_SLOTS * sizeof(double2)));
         MG_CUDA(cudaMallocHost(&c.pinned, 2 * RED_SLOTS * sizeof(double2)));
@@ -170,9 +170,12 @@ struct Ctx::Work {
     // fine-grid deflation of the eigensolver's shifted solves by the iterated vectors
     DevBuf QZ64all;              // Q z_j (FP64)
     DevBuf ZRall, QZRall;        // level-precision copies of z_j and Q z_j (mixed only)
-    DevBuf fdEinv, fdCoef;       // (Z^dag (Q - sigma) Z)^-1; coefficients c, d = E^-1 c, -sigma d
+    DevBuf AZRall;               // (Q - sigma) z_j of the active subset, level precision
+    DevBuf fdEinv, fdCoef;       // (Z_S^dag (Q - sigma) Z_S)^-1; coefficients c, d = E^-1 c
     std::vector<void *> QZ64, fdZ, fdQZ;   // FP64 Q z_j; level-precision z_j and Q z_j
-    std::vector<cpx<double>> Gz, Hz;       // Z^dag Z and Z^dag Q Z (row-major, k x k)
+    std::vector<void *> fdZs, fdAZs;       // the active subset: z_j and (Q - sigma) z_j
+    std::vector<cpx<double>> Gz, Hz;       // Z^dag Z and Z^dag Q Z (row-major, fd_n x fd_n)
+    int fd_n = 0;                          // maintained vectors (0: deflation off)
     int fd_k = 0;                          // vectors of the active deflation (0: off)
 };
 
@@ -215,6 +218,21 @@ void mg_alloc(Ctx &c) {
     w.defl_valid = false;
     w.Psrc = w.W;
     c.Dc.alloc((size_t)9 * c.nagg * 4 * ntv * ntv * 2 * c.level_bytes());
+    // periodic neighbours of every aggregate in the nine directions of the coarse stencil
+    std::vector<int> nbr((size_t)9 * c.nagg);
+    for (int s = 0; s < c.nagg; ++s) {
+        int x[4], rem = s;
+        for (int mu = 0; mu < 4; ++mu) { x[mu] = rem % c.cdims[mu]; rem /= c.cdims[mu]; }
+        nbr[s] = s;
+        for (int d = 1; d < 9; ++d) {
+            const int mu = (d - 1) / 2, step = (d & 1) ? 1 : -1;
+            int y[4] = {x[0], x[1], x[2], x[3]};
+            y[mu] = (y[mu] + step + c.cdims[mu]) % c.cdims[mu];
+            nbr[(size_t)d * c.nagg + s] = ((y[3] * c.cdims[2] + y[2]) * c.cdims[1] + y[1]) * c.cdims[0] + y[0];
+        }
+    }
+    c.cnbr.alloc(nbr.size() * sizeof(int));
+    MG_CUDA(cudaMemcpy(c.cnbr.p, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
 }
 
 void mg_free(Ctx &c) {
@@ -230,10 +248,11 @@ void mg_free(Ctx &c) {
     w.cgV.free(); w.cgRhs.free(); w.cgP.free();
     w.Wc.free(); w.AWc.free(); w.Edev.free(); w.Einv.free();
     w.Mextra.free(); w.Xall.free();
-    w.QZ64all.free(); w.ZRall.free(); w.QZRall.free(); w.fdEinv.free(); w.fdCoef.free();
+    w.QZ64all.free(); w.ZRall.free(); w.QZRall.free(); w.AZRall.free(); w.fdEinv.free(); w.fdCoef.free();
     delete c.work;
     c.work = nullptr;
     c.Dc.free();
+    c.cnbr.free();
 }
 
 void *mg_test_vector(Ctx &c, int j) { return c.work->W[j]; }
@@ -284,23 +303,48 @@ struct Hess {
     }
 };
 
-// Arnoldi step: w is orthogonalised against basis[0..j] (classical GS twice),
+// w <- w - X X^dag w for the orthonormal X[0..k) (classical Gram-Schmidt).  The
+// first pass also returns ||w||^2; a second pass runs only when the first one
+// removed more than half of ||w||^2 (the Daniel-Gragg-Kaufman-Stewart
+// criterion ||w'|| < ||w|| / sqrt 2), otherwise ||w'||^2 = ||w||^2 - sum |h_i|^2.
+// h[0..k) receives the summed coefficients; returns ||w'||^2.
+template <typename R>
+static double gs_dgks(Ctx &c, const void *const *X, int k, void *w, size_t n, cpx<double> *h) {
+    std::vector<const void *> Xw(X, X + k);
+    Xw.push_back(w);
+    blas_multidot<R>(c, Xw.data(), k + 1, w, n, dslot(c, H1));
+    if (k > 0) blas_multi_axpy<R>(c, w, X, k, dslot(c, H1), -1.0, n);
+    fetch(c, H1 + k + 1);
+    const double ww = hslot(c, H1 + k)->re;
+    double s = 0;
+    for (int i = 0; i < k; ++i) {
+        h[i] = *hslot(c, H1 + i);
+        MG_REQUIRE(finite(h[i]), MGEIG_EBREAKDOWN);
+        s += h[i].re * h[i].re + h[i].im * h[i].im;
+    }
+    MG_REQUIRE(std::isfinite(ww), MGEIG_EBREAKDOWN);
+    if (k == 0) return ww;
+    if (ww - s > 0.5 * ww) return ww - s;
+    blas_multidot<R>(c, X, k, w, n, dslot(c, H2));
+    blas_multi_axpy<R>(c, w, X, k, dslot(c, H2), -1.0, n);
+    blas_norm2<R>(c, w, n, dslot(c, HN));
+    fetch(c, HN + 1);
+    for (int i = 0; i < k; ++i) {
+        h[i] = h[i] + *hslot(c, H2 + i);
+        MG_REQUIRE(finite(h[i]), MGEIG_EBREAKDOWN);
+    }
+    return hslot(c, HN)->re;
+}
+
+// Arnoldi step: w is orthogonalised against basis[0..j] (gs_dgks),
 // Hessenberg column j filled (rows 0..j+1).  Returns the norm of w.
 template <typename R>
 static double arnoldi_step(Ctx &c, std::vector<void *> &basis, int j, void *w, size_t n, Hess &H) {
     std::vector<const void *> X(basis.begin(), basis.begin() + j + 1);
-    blas_multidot<R>(c, X.data(), j + 1, w, n, dslot(c, H1));
-    blas_multi_axpy<R>(c, w, X.data(), j + 1, dslot(c, H1), -1.0, n);
-    blas_multidot<R>(c, X.data(), j + 1, w, n, dslot(c, H2));
-    blas_multi_axpy<R>(c, w, X.data(), j + 1, dslot(c, H2), -1.0, n);
-    blas_norm2<R>(c, w, n, dslot(c, HN));
-    fetch(c, HN + 1);
-    for (int i = 0; i <= j; ++i) {
-        cpx<double> v = *hslot(c, H1 + i) + *hslot(c, H2 + i);
-        MG_REQUIRE(finite(v), MGEIG_EBREAKDOWN);
-        H.h(i, j) = v;
-    }
-    double nrm = std::sqrt(std::max(0.0, hslot(c, HN)->re));
+    std::vector<cpx<double>> h(j + 1);
+    const double w2 = gs_dgks<R>(c, X.data(), j + 1, w, n, h.data());
+    for (int i = 0; i <= j; ++i) H.h(i, j) = h[i];
+    double nrm = std::sqrt(std::max(0.0, w2));
     MG_REQUIRE(std::isfinite(nrm), MGEIG_EBREAKDOWN);
     H.h(j + 1, j) = cpx<double>(nrm);
     return nrm;
@@ -520,16 +564,9 @@ void mg_rebuild(Ctx &c) {
 static void orthonormalise(Ctx &c, std::vector<void *> &v, int n) {
     const size_t N = c.fine_ncpx();
     for (int j = 0; j < n; ++j) {
-        if (j > 0) {
-            std::vector<const void *> X(v.begin(), v.begin() + j);
-            for (int pass = 0; pass < 2; ++pass) {
-                blas_multidot<double>(c, X.data(), j, v[j], N, dslot(c, H1));
-                blas_multi_axpy<double>(c, v[j], X.data(), j, dslot(c, H1), -1.0, N);
-            }
-        }
-        blas_norm2<double>(c, v[j], N, dslot(c, HN));
-        fetch(c, HN + 1);
-        const double nrm = std::sqrt(hslot(c, HN)->re);
+        std::vector<const void *> X(v.begin(), v.begin() + j);
+        std::vector<cpx<double>> h(j);
+        const double nrm = std::sqrt(std::max(0.0, gs_dgks<double>(c, X.data(), j, v[j], N, h.data())));
         MG_REQUIRE(std::isfinite(nrm) && nrm > 0, MGEIG_EBREAKDOWN);
         blas_scale<double>(c, cpx<double>(1.0 / nrm), v[j], N);
     }
@@ -540,16 +577,9 @@ static void orthonormalise_from(Ctx &c, std::vector<void *> &v, int from) {
     const size_t N = c.fine_ncpx();
     const int n = (int)v.size();
     for (int j = from; j < n; ++j) {
-        if (j > 0) {
-            std::vector<const void *> X(v.begin(), v.begin() + j);
-            for (int pass = 0; pass < 2; ++pass) {
-                blas_multidot<double>(c, X.data(), j, v[j], N, dslot(c, H1));
-                blas_multi_axpy<double>(c, v[j], X.data(), j, dslot(c, H1), -1.0, N);
-            }
-        }
-        blas_norm2<double>(c, v[j], N, dslot(c, HN));
-        fetch(c, HN + 1);
-        const double nrm = std::sqrt(hslot(c, HN)->re);
+        std::vector<const void *> X(v.begin(), v.begin() + j);
+        std::vector<cpx<double>> h(j);
+        const double nrm = std::sqrt(std::max(0.0, gs_dgks<double>(c, X.data(), j, v[j], N, h.data())));
         MG_REQUIRE(std::isfinite(nrm) && nrm > 0, MGEIG_EBREAKDOWN);
         blas_scale<double>(c, cpx<double>(1.0 / nrm), v[j], N);
     }
@@ -644,7 +674,7 @@ void setup(Ctx &c, uint64_t seed) {
 static void fdefl_update(Ctx &c, const std::vector<void *> &M, int i) {
     Ctx::Work &w = *c.work;
     const size_t N = c.fine_ncpx();
-    const int k = w.fd_k;
+    const int k = w.fd_n;
     apply_fine<double>(c, MODE_QSIGMA, 0.0, M[i], w.QZ64[i]);
     std::vector<const void *> X(M.begin(), M.begin() + k);
     blas_multidot<double>(c, X.data(), k, M[i], N, dslot(c, H1));
@@ -669,15 +699,16 @@ static void fdefl_update(Ctx &c, const std::vector<void *> &M, int i) {
 }
 
 static void fdefl_all(Ctx &c, const std::vector<void *> &M) {
-    for (int i = 0; i < c.work->fd_k; ++i) fdefl_update(c, M, i);
+    for (int i = 0; i < c.work->fd_n; ++i) fdefl_update(c, M, i);
 }
 
 static void fdefl_begin(Ctx &c, const std::vector<void *> &M, int k) {
     Ctx::Work &w = *c.work;
-    w.fd_k = 0;
+    w.fd_n = w.fd_k = 0;
     if (!c.prm.fine_deflate) return;
     MG_REQUIRE(k >= 1 && k <= MAX_ITERATED, MGEIG_EINVAL);
     w.QZ64all.alloc(f64_bytes(c) * k);
+    w.AZRall.alloc(fR_bytes(c) * k);
     w.QZ64.resize(k);
     w.fdZ.resize(k);
     w.fdQZ.resize(k);
@@ -694,27 +725,54 @@ static void fdefl_begin(Ctx &c, const std::vector<void *> &M, int k) {
     w.fdCoef.alloc((size_t)3 * MAX_ITERATED * sizeof(double2));
     w.Gz.assign((size_t)k * k, cpx<double>());
     w.Hz.assign((size_t)k * k, cpx<double>());
-    w.fd_k = k;
+    w.fd_n = k;
     fdefl_all(c, M);
 }
 
 static void fdefl_end(Ctx &c) {
     Ctx::Work &w = *c.work;
-    w.fd_k = 0;
-    w.QZ64all.free(); w.ZRall.free(); w.QZRall.free(); w.fdEinv.free(); w.fdCoef.free();
-    w.QZ64.clear(); w.fdZ.clear(); w.fdQZ.clear();
+    w.fd_n = w.fd_k = 0;
+    w.QZ64all.free(); w.ZRall.free(); w.QZRall.free(); w.AZRall.free(); w.fdEinv.free(); w.fdCoef.free();
+    w.QZ64.clear(); w.fdZ.clear(); w.fdQZ.clear(); w.fdZs.clear(); w.fdAZs.clear();
 }
 
-// E^-1 = (Z^dag Q Z - sigma Z^dag Z)^-1 for the next solve
-static void fdefl_prepare(Ctx &c, double sigma) {
+// The deflation space of the solve for vector i at shift sigma: z_i and every
+// z_j whose Rayleigh quotient theta_j = <z_j, Q z_j> / <z_j, z_j> lies within
+// fine_deflate_radius of sigma (all iterated vectors when the radius is < 0);
+// E^-1 = (Z^dag Q Z - sigma Z^dag Z)^-1 and (Q - sigma) Z in the level precision.
+template <typename R>
+static void fdefl_prepare(Ctx &c, double sigma, int i) {
     Ctx::Work &w = *c.work;
-    const int k = w.fd_k;
-    if (!k) return;
+    const int nz = w.fd_n;
+    w.fd_k = 0;
+    if (!nz) return;
+    const size_t N = c.fine_ncpx();
+    const double rad = c.prm.fine_deflate_radius;
+    std::vector<int> S{i};
+    for (int j = 0; j < nz; ++j) {
+        if (j == i) continue;
+        const double theta = w.Hz[(size_t)j * nz + j].re / w.Gz[(size_t)j * nz + j].re;
+        if (rad < 0 || std::fabs(theta - sigma) <= rad) S.push_back(j);
+    }
+    const int k = (int)S.size();
     std::vector<cpx<double>> E((size_t)k * k), Ei;
-    for (size_t q = 0; q < E.size(); ++q) E[q] = w.Hz[q] - cpx<double>(sigma) * w.Gz[q];
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) {
+            const size_t q = (size_t)S[a] * nz + S[b];
+            E[(size_t)a * k + b] = w.Hz[q] - cpx<double>(sigma) * w.Gz[q];
+        }
     MG_REQUIRE(invert(k, E, Ei), MGEIG_EBREAKDOWN);
     MG_CUDA(cudaMemcpyAsync(w.fdEinv.p, Ei.data(), Ei.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+    w.fdZs.resize(k);
+    w.fdAZs.resize(k);
+    for (int a = 0; a < k; ++a) {
+        w.fdZs[a] = w.fdZ[S[a]];
+        w.fdAZs[a] = static_cast<char *>(w.AZRall.p) + fR_bytes(c) * a;
+        blas_copy<R>(c, w.fdQZ[S[a]], w.fdAZs[a], N);
+        blas_axpy<R>(c, cpx<double>(-sigma), w.fdZs[a], w.fdAZs[a], N);
+    }
     sync(c);
+    w.fd_k = k;
 }
 
 // z = M r for the FP64 Arnoldi vector v (z in the level precision R): the
@@ -727,16 +785,15 @@ static void precondition(Ctx &c, double sigma, const void *v64, void *z) {
     if (sizeof(R) == 4) convert_f64_to_f32(c, v64, w.rR.p, n);
     else if (k) blas_copy<double>(c, v64, w.rR.p, n);
     const void *r = (sizeof(R) == 4 || k) ? w.rR.p : v64;
+    cpx<double> *cf = w.fdCoef.as<cpx<double>>();
+    cpx<double> *d = cf + MAX_ITERATED, *unused = cf + 2 * MAX_ITERATED;
     if (k) {
-        cpx<double> *cf = w.fdCoef.as<cpx<double>>();
-        cpx<double> *d = cf + MAX_ITERATED, *sd = cf + 2 * MAX_ITERATED;
-        blas_multidot<R>(c, (const void *const *)w.fdZ.data(), k, w.rR.p, n, cf);          // Z^dag r
-        small_gemv(c, w.fdEinv.as<cpx<double>>(), k, cf, -sigma, d, sd);                   // d, -sigma d
-        blas_multi_axpy<R>(c, w.rR.p, (const void *const *)w.fdQZ.data(), k, d, -1.0, n);  // r -= Q Z d
-        blas_multi_axpy<R>(c, w.rR.p, (const void *const *)w.fdZ.data(), k, sd, -1.0, n);  // r += sigma Z d
+        blas_multidot<R>(c, (const void *const *)w.fdZs.data(), k, w.rR.p, n, cf);           // Z^dag r
+        small_gemv(c, w.fdEinv.as<cpx<double>>(), k, cf, 0.0, d, unused);                   // d = E^-1 Z^dag r
+        blas_multi_axpy<R>(c, w.rR.p, (const void *const *)w.fdAZs.data(), k, d, -1.0, n);  // r -= (Q - sigma) Z d
     }
     mg_cycle<R>(c, sigma, r, z);
-    if (k) blas_multi_axpy<R>(c, z, (const void *const *)w.fdZ.data(), k, w.fdCoef.as<cpx<double>>() + MAX_ITERATED, 1.0, n);
+    if (k) blas_multi_axpy<R>(c, z, (const void *const *)w.fdZs.data(), k, d, 1.0, n);      // z += Z d
 }
 
 // ---------------------------------------------------------------------------
@@ -972,7 +1029,8 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             const double dls = std::fabs(lam[i] - sigma);
             const double tau = (is_guard || dls == 0) ? c.prm.solve_tol
                                                       : std::min(c.prm.solve_tol, std::max(0.1 * tol / dls, 1e-12));
-            fdefl_prepare(c, sigma);
+            if (c.mixed()) fdefl_prepare<float>(c, sigma, i);
+            else fdefl_prepare<double>(c, sigma, i);
             int rc = fgmres_solve(c, sigma, M[i], w.x64.p, tau,
                                   is_guard ? std::min(c.prm.guard_maxiter, c.prm.outer_maxiter) : c.prm.outer_maxiter);
             if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
@@ -980,20 +1038,15 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             std::vector<const void *> X;
             for (int j = 0; j < n_eig; ++j)
                 if (j < i || (rr && locked[j] && j != i)) X.push_back(M[j]);
-            if (!X.empty()) {
-                for (int pass = 0; pass < 2; ++pass) {
-                    blas_multidot<double>(c, X.data(), (int)X.size(), w.x64.p, N, dslot(c, H1));
-                    blas_multi_axpy<double>(c, w.x64.p, X.data(), (int)X.size(), dslot(c, H1), -1.0, N);
-                }
-            }
-            blas_norm2<double>(c, w.x64.p, N, dslot(c, HN));
-            fetch(c, HN + 1);
-            const double nrm = std::sqrt(hslot(c, HN)->re);
+            std::vector<cpx<double>> hx(X.size());
+            const double nrm = std::sqrt(std::max(0.0, gs_dgks<double>(c, X.data(), (int)X.size(), w.x64.p, N,
+                                                                          hx.data())));
             MG_REQUIRE(std::isfinite(nrm) && nrm > 0, MGEIG_EBREAKDOWN);
             blas_scale<double>(c, cpx<double>(1.0 / nrm), w.x64.p, N);
             blas_copy<double>(c, w.x64.p, M[i], N);
             if (i < ntv) mg_rebuild(c);   // P holds the first N_tv iterated vectors
-            if (w.fd_k) fdefl_update(c, M, i);
+            w.fd_k = 0;   // the solve is over
+            if (w.fd_n) fdefl_update(c, M, i);
             auto le = rayleigh(c, M[i]);
             lam[i] = le.first;
             eps[i] = le.second;
