@@ -35,6 +35,12 @@ WORKLOAD = dict(
     dims=[16, 16, 16, 32], eps=0.2, seed=1002, csw=1.9, n_eig=20, tol=1e-10,
 )
 COUNTS_FILE = os.path.join(ROOT, "bench_counts.json")
+# library timer classes that are one kernel each (the BLAS classes are several)
+SINGLE_KERNEL_CLASSES = ("coarse_gmres", "stencil_f64", "stencil_f32", "sap_f32", "sap_f64", "restrict", "prolong",
+                         "coarse_apply", "coarse_build", "interp_build")
+# DRAM bytes (read + write) per launch from an ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum); None where none was taken
+DRAM_BYTES_PER_LAUNCH = {}
 
 
 def load_m0() -> float:
@@ -222,14 +228,20 @@ def run_gpu(args):
     ctx = make_ctx(MIXED)
     ctx.load_gauge_dev(U_dev.data_ptr())
     sten = stencil_microbench(ctx, dims, flush, peaks()["hbm"])
-    for _ in range(args.warmup):
+    # the last warm-up step records every kernel class (the per-class breakdown);
+    # the timed steps record events for the dominant single kernel only
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            ctx.set_timing(True)
         step(ctx, w["seed"])
-    ctx.set_timing(True)
+    kt = ctx.kernel_times()
+    top = max((k for k in SINGLE_KERNEL_CLASSES if k in kt), key=lambda k: kt[k]["ms"])
+    ctx.set_timing_classes([top])
     n_launch0 = ctx.launch_count()
     with ClockSampler(local) as clk:
         t_mixed, outs = timed(ctx, args.steps, w["seed"])
     launches = ctx.launch_count() - n_launch0
-    kt = ctx.kernel_times()
+    kt_top = ctx.kernel_times()[top]
     ctx.set_timing(False)
     lam, res, st = outs[-1]
     t_mixed = max_over_ranks(dist, t_mixed, dev)
@@ -264,11 +276,11 @@ def run_gpu(args):
     if rank != 0:
         return
     pk = peaks()
-    # dominant kernel class by device time inside the timed region
-    top = max(kt, key=lambda k: kt[k]["ms"])
-    achieved = kt[top]["bytes"] / (kt[top]["ms"] / 1e3) / 1e9 if kt[top]["ms"] > 0 else None
+    # the dominant single kernel, its algorithmic bytes over its event-timed
+    # duration inside the timed region
+    achieved = kt_top["bytes"] / (kt_top["ms"] / 1e3) / 1e9 if kt_top["ms"] > 0 else None
     with open(COUNTS_FILE + ".new", "w") as f:
-        json.dump(dict(workload=w["workload"], steps=args.steps, kernels=kt, stats=st), f, indent=1)
+        json.dump(dict(workload=w["workload"], steps=1, kernels=kt, stats=st), f, indent=1)
     value = t_mixed / (args.steps * ws)
     line = dict(
         metric=METRIC, value=value, unit="s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
@@ -283,14 +295,18 @@ def run_gpu(args):
                     mg_cycles=st["mg_cycles"], coarse_iters=st["coarse_iters"]),
         stencil=dict(sten, l2="flushed before every launch", lattice=w["dims"]),
         roofline=dict(bound="hbm", kernel=top, achieved=achieved, peak=pk["hbm"], unit="GB/s",
-                      frac=(achieved / pk["hbm"]) if achieved else None, traffic=None,
-                      peak_src=f"{pk['src']} hbm_gbs"),
+                      frac=(achieved / pk["hbm"]) if achieved else None,
+                      traffic=DRAM_BYTES_PER_LAUNCH.get(top),
+                      launches=kt_top["launches"], ms=kt_top["ms"],
+                      bytes_per_launch=kt_top["bytes"] / max(1, kt_top["launches"]),
+                      peak_src=f"{pk['src']} hbm_gbs (burst copy)"),
         e2e=dict(value=t_e2e, unit="s", h2d_bytes_per_step=int(U.nbytes),
                  d2h_bytes_per_step=int(V_e.nbytes + lam_e.nbytes + res_e.nbytes)),
         gpu_launches=int(launches),
         clocks=clk.summary(),
         kernels={k: dict(launches=v["launches"], ms=round(v["ms"], 3), gbs=(v["bytes"] / v["ms"] / 1e6) if v["ms"] else None)
                  for k, v in kt.items() if v["launches"]},
+        kernels_note="per-class device time of one step (the last warm-up step, every class timed)",
     )
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess(kt_counts=kt, stats=st, steps=args.steps)

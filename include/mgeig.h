@@ -282,6 +282,11 @@ int mgeig_eigensolve(mgeig_ctx *ctx, int n_eig, double tol, double *evals, doubl
  * (the bytes a perfect kernel would read and write once); names[k] is a static
  * string.  Returns the number of classes, or a negative status. */
 int mgeig_set_timing(mgeig_ctx *ctx, int on);
+/* As mgeig_set_timing(ctx, 1), but only the kernel classes whose bit is set in
+ * mask (bit k = class k of mgeig_kernel_times) record CUDA events, so that one
+ * class can be timed with little overhead on the rest; mask 0 switches timing
+ * off.  The paper has no counterpart. */
+int mgeig_set_timing_classes(mgeig_ctx *ctx, unsigned int mask);
 int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms,
                        double *bytes, const char **names);
 

@@ -91,6 +91,7 @@ def load():
         "mgeig_solve": (I, [P, D, P, P, D, C.POINTER(Stats)]),
         "mgeig_eigensolve": (I, [P, I, D, P, P, P, C.POINTER(Stats)]),
         "mgeig_set_timing": (I, [P, I]),
+        "mgeig_set_timing_classes": (I, [P, C.c_uint]),
         "mgeig_kernel_times": (I, [P, I, P, P, P, P]),
         "mgeig_get_stream": (I, [P, C.POINTER(P)]),
         "mgeig_get_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
@@ -308,6 +309,14 @@ class Context:
 
     def set_timing(self, on: bool):
         self._check("mgeig_set_timing", self.lib.mgeig_set_timing(self._h, 1 if on else 0))
+
+    def set_timing_classes(self, names):
+        """Time only the named kernel classes (names as in kernel_times())."""
+        order = list(self.kernel_times())
+        mask = 0
+        for n in names:
+            mask |= 1 << order.index(n)
+        self._check("mgeig_set_timing_classes", self.lib.mgeig_set_timing_classes(self._h, C.c_uint(mask)))
 
     def kernel_times(self):
         n = 16

@@ -528,6 +528,16 @@ int mgeig_set_timing(mgeig_ctx *ctx, int on) {
     return guarded(ctx, [&](Ctx &c) {
         c.timer.reset();
         c.timer.on = on != 0;
+        c.timer.mask = ~0u;
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_set_timing_classes(mgeig_ctx *ctx, unsigned int mask) {
+    return guarded(ctx, [&](Ctx &c) {
+        c.timer.reset();
+        c.timer.on = mask != 0;
+        c.timer.mask = mask;
         return MGEIG_OK;
     });
 }

@@ -67,6 +67,7 @@ enum KernelClass {
 
 struct Timer {
     bool on = false;
+    unsigned int mask = ~0u;            // kernel classes that record events while on
     cudaStream_t stream = nullptr;
     long long launches[K_NCLASS] = {};
     double ms[K_NCLASS] = {};
@@ -87,11 +88,11 @@ struct Timer {
 struct TimeScope {
     Timer &t; int cls; double bytes; cudaEvent_t a = nullptr;
     TimeScope(Timer &t_, int cls_, double bytes_) : t(t_), cls(cls_), bytes(bytes_) {
-        if (t.on) a = t.begin(cls);
+        if (t.on && (t.mask >> cls & 1u)) a = t.begin(cls);
         t.launches[cls] += 1;
         t.total_bytes[cls] += bytes_;
     }
-    ~TimeScope() { if (t.on) t.end(cls, a, bytes); else t.bytes[cls] = bytes; }
+    ~TimeScope() { if (a) t.end(cls, a, bytes); else t.bytes[cls] = bytes; }
 };
 
 struct Ctx;
