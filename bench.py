@@ -40,7 +40,13 @@ SINGLE_KERNEL_CLASSES = ("coarse_gmres", "stencil_f64", "stencil_f32", "sap_f32"
                          "coarse_apply", "coarse_build", "interp_build")
 # DRAM bytes (read + write) per launch from an ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where none was taken
-DRAM_BYTES_PER_LAUNCH = {}
+DRAM_BYTES_PER_LAUNCH = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:coarse_gmres -s 20 -c 3 on
+    # `python -m paper_1509_06865_gb300.profile_case --case eig16` (same 16^3x32 coarse grid): 66.0 MB read +
+    # 0.17 MB written per launch, whatever the number of GMRES steps (the coarse operator is read from DRAM once per
+    # solve and then served by L2)
+    "coarse_gmres": 66.17e6,
+}
 
 
 def load_m0() -> float:
@@ -309,7 +315,7 @@ def run_gpu(args):
         kernels_note="per-class device time of one step (the last warm-up step, every class timed)",
     )
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_subprocess(kt_counts=kt, stats=st, steps=args.steps)
+        line["cpu_baseline"] = cpu_baseline_subprocess(kt_counts=kt, stats=st, steps=1)   # kt covers one step
     print(json.dumps(line), flush=True)
 
 

@@ -24,6 +24,17 @@ template <> struct V2<float> { typedef float2 T; };
 
 struct PtrPack { const void *p[CHUNK]; };
 
+// FP32 arrays of an even number of complex values on 16-byte boundaries are
+// processed two values per float4 access
+template <typename R>
+static bool vec4_ok(const PtrPack &pk, int k, const void *y, size_t n) {
+    if (sizeof(R) != 4 || (n & 1)) return false;
+    if (reinterpret_cast<uintptr_t>(y) & 15) return false;
+    for (int j = 0; j < k; ++j)
+        if (reinterpret_cast<uintptr_t>(pk.p[j]) & 15) return false;
+    return true;
+}
+
 static int red_grid(size_t n) {
     size_t b = (n + RED_THREADS * 4 - 1) / (RED_THREADS * 4);
     if (b < 1) b = 1;
@@ -60,13 +71,32 @@ __device__ __forceinline__ void block_reduce_store(double (&re)[MAXV], double (&
 
 template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) multidot_kernel(PtrPack X, int k, const void *__restrict__ yv, size_t n,
-                                                               double2 *__restrict__ partial, size_t pstride) {
+                                                               double2 *__restrict__ partial, size_t pstride, bool vec4) {
     typedef typename V2<R>::T T;
     const T *y = static_cast<const T *>(yv);
     constexpr int C = Chunk<R>::n;
     R ar[C], ai[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) { ar[j] = 0; ai[j] = 0; }
+    if constexpr (sizeof(R) == 4) {
+        if (vec4) {   // two complex values per 16-byte load (n even, 16-byte aligned arrays)
+            const float4 *y4 = static_cast<const float4 *>(yv);
+            for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x) {
+                const float4 b = y4[i];
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    if (j < k) {
+                        const float4 a = static_cast<const float4 *>(X.p[j])[i];
+                        ar[j] = fmaf(a.x, b.x, ar[j]); ar[j] = fmaf(a.y, b.y, ar[j]);
+                        ar[j] = fmaf(a.z, b.z, ar[j]); ar[j] = fmaf(a.w, b.w, ar[j]);
+                        ai[j] = fmaf(a.x, b.y, ai[j]); ai[j] = fmaf(-a.y, b.x, ai[j]);
+                        ai[j] = fmaf(a.z, b.w, ai[j]); ai[j] = fmaf(-a.w, b.z, ai[j]);
+                    }
+                }
+            }
+            n = 0;   // the scalar loop below has nothing left to do
+        }
+    }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         T b = y[i];
 #pragma unroll
@@ -140,7 +170,8 @@ void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n,
         PtrPack pk{};
         const int kk = k - j0 < C ? k - j0 : C;
         for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
-        multidot_kernel<R><<<nb, RED_THREADS, 0, c.stream>>>(pk, kk, y, n, partial_ptr(c) + (size_t)j0 * pstride, pstride);
+        multidot_kernel<R><<<nb, RED_THREADS, 0, c.stream>>>(pk, kk, y, n, partial_ptr(c) + (size_t)j0 * pstride, pstride,
+                                                             vec4_ok<R>(pk, kk, y, n));
         MG_CHECK_LAUNCH();
     }
     finalize_kernel<<<k, 128, 0, c.stream>>>(partial_ptr(c), pstride, nb, reinterpret_cast<double2 *>(d_out));
@@ -170,7 +201,7 @@ void blas_resid_norm2(Ctx &c, const void *qv, const void *v, const cpx<double> *
 // y += sign * sum_j coef[j] X_j
 template <typename R>
 __global__ void multi_axpy_kernel(void *__restrict__ yv, PtrPack X, int k, const double2 *__restrict__ coef, double sign,
-                                  size_t n) {
+                                  size_t n, bool vec4) {
     typedef typename V2<R>::T T;
     T *y = static_cast<T *>(yv);
     constexpr int C = Chunk<R>::n;
@@ -179,6 +210,26 @@ __global__ void multi_axpy_kernel(void *__restrict__ yv, PtrPack X, int k, const
     for (int j = 0; j < C; ++j) {
         if (j < k) { double2 t = coef[j]; cr[j] = (R)(sign * t.x); ci[j] = (R)(sign * t.y); }
         else { cr[j] = 0; ci[j] = 0; }
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (vec4) {   // two complex values per 16-byte access
+            float4 *y4 = static_cast<float4 *>(yv);
+            for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x) {
+                float4 acc = y4[i];
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    if (j < k) {
+                        const float4 a = static_cast<const float4 *>(X.p[j])[i];
+                        acc.x = fmaf(cr[j], a.x, acc.x); acc.x = fmaf(-ci[j], a.y, acc.x);
+                        acc.y = fmaf(cr[j], a.y, acc.y); acc.y = fmaf(ci[j], a.x, acc.y);
+                        acc.z = fmaf(cr[j], a.z, acc.z); acc.z = fmaf(-ci[j], a.w, acc.z);
+                        acc.w = fmaf(cr[j], a.w, acc.w); acc.w = fmaf(ci[j], a.z, acc.w);
+                    }
+                }
+                y4[i] = acc;
+            }
+            return;
+        }
     }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         T acc = y[i];
@@ -208,8 +259,9 @@ void blas_multi_axpy(Ctx &c, void *y, const void *const *X, int k, const cpx<dou
         PtrPack pk{};
         const int kk = k - j0 < C ? k - j0 : C;
         for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
-        multi_axpy_kernel<R><<<ew_grid(n), 256, 0, c.stream>>>(y, pk, kk, reinterpret_cast<const double2 *>(d_coef + j0),
-                                                               sign, n);
+        const bool v4 = vec4_ok<R>(pk, kk, y, n);
+        multi_axpy_kernel<R><<<ew_grid(v4 ? n / 2 : n), 256, 0, c.stream>>>(
+            y, pk, kk, reinterpret_cast<const double2 *>(d_coef + j0), sign, n, v4);
         MG_CHECK_LAUNCH();
     }
 }

@@ -126,17 +126,37 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
         cpx<R> acc0, acc1;
         if (t < r1) {
             const int site = t / n2, row = t % n2;
-#pragma unroll 3
-            for (int d = 0; d < 9; ++d) {
-                const int nb = __ldg(a.nbr + (size_t)d * a.nagg + site);
-                const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
-                const cpx<R> *xb = v + (size_t)nb * n2;
-                int j = q;
-                for (; j + TPR < n2; j += 2 * TPR) {
-                    cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
-                    cmac(acc1, blk[(size_t)(j + TPR) * n2], ldcg(xb + j + TPR));
+            if constexpr (sizeof(R) == 4) {
+                // n2 <= 2 * CG_MAXK = 48: a lane's (at most 6) columns of one block are
+                // loaded before they are used, so their L2 latencies overlap
+                constexpr int U = (2 * CG_MAXK + TPR - 1) / TPR;
+                for (int d = 0; d < 9; ++d) {
+                    const int nb = __ldg(a.nbr + (size_t)d * a.nagg + site);
+                    const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
+                    const cpx<R> *xb = v + (size_t)nb * n2;
+                    cpx<R> bv[U], xv[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int j = q + u * TPR;
+                        if (j < n2) { bv[u] = blk[(size_t)j * n2]; xv[u] = ldcg(xb + j); }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (q + u * TPR < n2) cmac((u & 1) ? acc1 : acc0, bv[u], xv[u]);
                 }
-                if (j < n2) cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+            } else {
+#pragma unroll 3
+                for (int d = 0; d < 9; ++d) {
+                    const int nb = __ldg(a.nbr + (size_t)d * a.nagg + site);
+                    const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
+                    const cpx<R> *xb = v + (size_t)nb * n2;
+                    int j = q;
+                    for (; j + TPR < n2; j += 2 * TPR) {
+                        cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+                        cmac(acc1, blk[(size_t)(j + TPR) * n2], ldcg(xb + j + TPR));
+                    }
+                    if (j < n2) cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+                }
             }
         }
         cpx<R> acc = acc0 + acc1;
