@@ -234,6 +234,14 @@ def run_gpu(args):
     ctx = make_ctx(MIXED)
     ctx.load_gauge_dev(U_dev.data_ptr())
     sten = stencil_microbench(ctx, dims, flush, peaks()["hbm"])
+    # the same stencil on the 32^3 x 64 lattice of the larger workloads (unit links:
+    # the stencil's memory traffic does not depend on the link values)
+    big = (32, 32, 32, 64)
+    ctxb = Context(big, device=local)
+    ctxb.set_params(m0=m0, csw=w["csw"], n_tv=20, precision=MIXED)
+    ctxb.load_gauge(synth.unit_gauge(big))
+    sten_big = stencil_microbench(ctxb, big, flush, peaks()["hbm"], n=20)
+    ctxb.close()
     # the last warm-up step records every kernel class (the per-class breakdown);
     # the timed steps record events for the dominant single kernel only
     for i in range(args.warmup):
@@ -299,7 +307,8 @@ def run_gpu(args):
         result=dict(lambda_min=float(lam[0]), lambda_max=float(lam[-1]), max_resid=float(max(res)),
                     sweeps=st["sweeps"], solves=st["solves"], outer_iters=st["outer_iters"],
                     mg_cycles=st["mg_cycles"], coarse_iters=st["coarse_iters"]),
-        stencil=dict(sten, l2="flushed before every launch", lattice=w["dims"]),
+        stencil=dict(sten, l2="flushed before every launch", lattice=w["dims"],
+                     lattice_32x32x32x64=sten_big),
         roofline=dict(bound="hbm", kernel=top, achieved=achieved, peak=pk["hbm"], unit="GB/s",
                       frac=(achieved / pk["hbm"]) if achieved else None,
                       traffic=DRAM_BYTES_PER_LAUNCH.get(top),

@@ -271,7 +271,9 @@ __global__ void __launch_bounds__(128) wilson_clover_kernel(Geom g, const void *
     cpx<R> up[6], lo[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) { up[k] = cpx<R>(); lo[k] = cpx<R>(); }
-#pragma unroll 1
+    // unrolled: the coordinates, strides and gamma structure of each direction are
+    // compile-time, nothing is indexed at run time (no local-memory frame)
+#pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
         int ph;
         cpx<R> u[9], psi[12];
