@@ -51,9 +51,9 @@ DRAM_BYTES_PER_LAUNCH = {
 
 def load_m0() -> float:
     with open(os.path.join(ROOT, "workloads.json")) as f:
-        m0 = json.load(f)["config2"]["m0"]
+        m0 = json.load(f)["bench_16x16x16x32"]["m0"]
     if m0 is None:
-        raise RuntimeError("workloads.json: config2 m0 not tuned yet")
+        raise RuntimeError("workloads.json: m0 of the 16^3x32 workload not tuned yet")
     return float(m0)
 
 

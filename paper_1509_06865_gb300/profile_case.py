@@ -28,7 +28,7 @@ def main():
     from paper_1509_06865_gb300 import MIXED, Context
 
     with open(os.path.join(ROOT, "workloads.json")) as f:
-        cfg = json.load(f)["config2"]
+        cfg = json.load(f)["bench_16x16x16x32"]
     dims = tuple(cfg["dims"])
     U = synth.gauge_field(dims, cfg["eps"], cfg["seed"])
     ctx = Context(dims)

@@ -12,12 +12,12 @@ from oracle import dense, dirac
 
 pytestmark = pytest.mark.gpu
 
-CFG1 = dict(dims=(4, 4, 4, 4), eps=0.3, seed=1001, m0=-0.4, csw=1.0, n_eig=4)
+DENSE4 = dict(dims=(4, 4, 4, 4), eps=0.3, seed=1001, m0=-0.4, csw=1.0, n_eig=4)
 
 
 @pytest.fixture(scope="module")
 def ref():
-    c = CFG1
+    c = DENSE4
     U = synth.gauge_field(c["dims"], c["eps"], c["seed"])
     op = dirac.WilsonClover(U, c["m0"], c["csw"])
     Qm = dense.operator_matrix(op.Q, c["dims"])
@@ -27,10 +27,10 @@ def ref():
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("smoother", [0, 1], ids=["sap", "gmres"])
-def test_eigensolve_config1(ref, precision, smoother):
+def test_eigensolve_4x4x4x4_vs_dense(ref, precision, smoother):
     from paper_1509_06865_gb300 import Context
     U, op, Qm, w, v = ref
-    c = CFG1
+    c = DENSE4
     ctx = Context(c["dims"])
     ctx.set_params(m0=c["m0"], csw=c["csw"], agg=(2, 2, 2, 2), n_tv=8, sap_block=(2, 2, 2, 2),
                    precision=precision, smoother=smoother)
@@ -67,7 +67,7 @@ def test_eigensolve_config1(ref, precision, smoother):
 def test_fgmres_solve_matches_dense(ref):
     from paper_1509_06865_gb300 import Context
     U, op, Qm, w, v = ref
-    c = CFG1
+    c = DENSE4
     ctx = Context(c["dims"])
     ctx.set_params(m0=c["m0"], csw=c["csw"], agg=(2, 2, 2, 2), n_tv=8, sap_block=(2, 2, 2, 2))
     ctx.load_gauge(U)

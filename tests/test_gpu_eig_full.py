@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 
 DIMS = (16, 16, 16, 32)
 WORKLOADS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "workloads.json")
-CFG2 = json.load(open(WORKLOADS))["config2"]
+BENCH16 = json.load(open(WORKLOADS))["bench_16x16x16x32"]
 
 
 def test_free_field_closed_form():
@@ -50,10 +50,10 @@ def test_free_field_closed_form():
         assert np.linalg.norm(wrong) <= 1e-8                             # gamma5 v = sign(lambda) v
 
 
-@pytest.mark.skipif(CFG2["m0"] is None, reason="tuned m0 not recorded")
-def test_config2_random_field_certified_by_oracle():
+@pytest.mark.skipif(BENCH16["m0"] is None, reason="tuned m0 not recorded")
+def test_16x16x16x32_random_field_certified_by_oracle():
     from paper_1509_06865_gb300 import FP64, MIXED, Context
-    cfg = CFG2
+    cfg = BENCH16
     U = synth.gauge_field(DIMS, cfg["eps"], cfg["seed"])
     out = {}
     for prec in (MIXED, FP64):

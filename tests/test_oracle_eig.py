@@ -7,11 +7,11 @@ import numpy as np
 import synth
 from oracle import dense, dirac, mg, rqi
 
-CFG1 = dict(dims=(4, 4, 4, 4), eps=0.3, seed=1001, m0=-0.4, csw=1.0, n_eig=4)
+DENSE4 = dict(dims=(4, 4, 4, 4), eps=0.3, seed=1001, m0=-0.4, csw=1.0, n_eig=4)
 
 
 def test_rqi_matches_dense_eigh():
-    c = CFG1
+    c = DENSE4
     op = dirac.WilsonClover(synth.gauge_field(c["dims"], c["eps"], c["seed"]), c["m0"], c["csw"])
     params = dict(mg.DEFAULT_PARAMS, agg=(2, 2, 2, 2), ntv=8, sap_block=(2, 2, 2, 2))
     W0 = synth.uniform_vectors(c["dims"], 8, c["seed"])
