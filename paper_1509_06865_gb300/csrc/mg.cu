@@ -496,6 +496,7 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
         cpx<R> up[6], lo[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) { up[k] = cpx<R>(); lo[k] = cpx<R>(); }
+#pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
             int ph;
             cpx<R> u[9], psi[12];
@@ -532,7 +533,9 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
             cpx<R> up[6], lo[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) { up[k] = cpx<R>(); lo[k] = cpx<R>(); }
+#pragma unroll
             for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
                 for (int f = 0; f < 2; ++f) {
                     const bool fwd = f == 0;
                     const int lm = lc[mu] + (fwd ? 1 : -1);
