@@ -255,6 +255,17 @@ constexpr int CB_THREADS = 256;
 constexpr int CB_CHUNK = 8;   // fine sites staged per step
 constexpr int CB_MAXO = 9;    // outputs per thread: (2*24)^2 / 256
 
+// keeps chirality cp of a spinor (components 6 cp .. 6 cp + 5) and zeroes the
+// other, with compile-time indices only
+template <typename R>
+__device__ __forceinline__ void zero_other_chirality(cpx<R> psi[12], int cp) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (cp == 0) psi[6 + k] = cpx<R>();
+        else psi[k] = cpx<R>();
+    }
+}
+
 // directional fine operator applied to column (cp, jp) of P at fine site s:
 // d = 0: local term + hops that stay inside the aggregate; d = 1 + 2mu / 2 + 2mu:
 // the single hop leaving the aggregate through its upper / lower mu face.
@@ -265,7 +276,9 @@ __device__ void directional_column(const Geom &g, const AggGeom &A, const void *
     cpx<R> up[6], lo[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) { up[k] = cpx<R>(); lo[k] = cpx<R>(); }
+#pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
         for (int f = 0; f < 2; ++f) {
             const bool fwd = f == 0;
             const int lm = c[mu] % A.agg[mu];
@@ -277,8 +290,7 @@ __device__ void directional_column(const Geom &g, const AggGeom &A, const void *
             cpx<R> u[9], psi[12];
             Gauge<R>::load(U, V, mu, fwd ? s : n, u);
             Spinor<R>::load(Pj, V, n, psi);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) psi[(1 - cp) * 6 + k] = cpx<R>();
+            zero_other_chirality(psi, cp);
             hop_accumulate<R>(mu, fwd, u, psi, (R)ph, up, lo);
         }
     }
@@ -286,8 +298,7 @@ __device__ void directional_column(const Geom &g, const AggGeom &A, const void *
     if (d == 0) {
         cpx<R> psi[12];
         Spinor<R>::load(Pj, V, s, psi);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) psi[(1 - cp) * 6 + k] = cpx<R>();
+        zero_other_chirality(psi, cp);
         clover_apply<R>(clov, V, s, psi, out);
     } else {
 #pragma unroll
@@ -321,15 +332,21 @@ __global__ void __launch_bounds__(CB_THREADS) coarse_build_kernel(Geom g, AggGeo
             // face site enumeration: local index over the face, expanded to the aggregate
             int l = base + sl;
             if (d != 0) {
-                // build local coordinates with l_mu fixed
-                int rem = l, lc[4];
+                // local coordinates with l_mu fixed (no run-time indexed arrays)
+                int rem = l, ln = 0, st = 1;
+#pragma unroll
                 for (int nu = 0; nu < 4; ++nu) {
-                    if (nu == mu) continue;
-                    lc[nu] = rem % A.agg[nu];
-                    rem /= A.agg[nu];
+                    int x;
+                    if (nu == mu) {
+                        x = (d & 1) ? A.agg[nu] - 1 : 0;
+                    } else {
+                        x = rem % A.agg[nu];
+                        rem /= A.agg[nu];
+                    }
+                    ln += x * st;
+                    st *= A.agg[nu];
                 }
-                lc[mu] = (d & 1) ? A.agg[mu] - 1 : 0;
-                l = ((lc[3] * A.agg[2] + lc[2]) * A.agg[1] + lc[1]) * A.agg[0] + lc[0];
+                l = ln;
             }
             int lc[4], c[4];
             const int s = agg_site(g, A, a, l, lc);
@@ -393,23 +410,15 @@ void build_coarse(Ctx &c, const void *const *P, void *Dc) {
 // dform = 0: y = (gamma5^c D_c - sigma) x = (Q_c - sigma) x
 // dform = 1: y = (D_c - sigma gamma5^c) x = gamma5^c (Q_c - sigma) x
 template <typename R>
-__global__ void coarse_apply_kernel(AggGeom A, int ntv, const cpx<R> *__restrict__ Dc, R sigma,
-                                    const cpx<R> *__restrict__ x, cpx<R> *__restrict__ y, int dform) {
+__global__ void coarse_apply_kernel(AggGeom A, int ntv, const cpx<R> *__restrict__ Dc, const int *__restrict__ nbr,
+                                    R sigma, const cpx<R> *__restrict__ x, cpx<R> *__restrict__ y, int dform) {
     const int n2 = 2 * ntv;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)A.n * n2) return;
     const int a = (int)(t / n2), row = (int)(t % n2);
-    int ac[4], rem = a;
-    for (int mu = 0; mu < 4; ++mu) { ac[mu] = rem % A.cdims[mu]; rem /= A.cdims[mu]; }
     cpx<R> acc;
     for (int d = 0; d < 9; ++d) {
-        int b = a;
-        if (d > 0) {
-            const int mu = (d - 1) / 2, step = (d & 1) ? 1 : -1;
-            int bc[4] = {ac[0], ac[1], ac[2], ac[3]};
-            bc[mu] = (bc[mu] + step + A.cdims[mu]) % A.cdims[mu];
-            b = ((bc[3] * A.cdims[2] + bc[2]) * A.cdims[1] + bc[1]) * A.cdims[0] + bc[0];
-        }
+        const int b = __ldg(nbr + (size_t)d * A.n + a);   // neighbour aggregate in direction d
         const cpx<R> *blk = Dc + ((size_t)d * A.n + a) * n2 * n2 + row;
         const cpx<R> *xb = x + (size_t)b * n2;
         for (int j = 0; j < n2; ++j) cmac(acc, blk[(size_t)j * n2], xb[j]);
@@ -445,7 +454,9 @@ void coarse_apply(Ctx &c, const void *Dc, double sigma, const void *x, void *y, 
     const int ntv = c.prm.n_tv;
     const size_t n = (size_t)A.n * 2 * ntv;
     TimeScope ts(c.timer, K_COARSE_APPLY, (double)A.n * (9.0 * 4 * ntv * ntv + 20.0 * ntv) * sizeof(cpx<R>));
-    coarse_apply_kernel<R><<<grid_for(n, 128), 128, 0, c.stream>>>(A, ntv, static_cast<const cpx<R> *>(Dc), (R)sigma,
+    MG_REQUIRE(c.cnbr.p != nullptr, MGEIG_ENOTSETUP);
+    coarse_apply_kernel<R><<<grid_for(n, 128), 128, 0, c.stream>>>(A, ntv, static_cast<const cpx<R> *>(Dc),
+                                                                   c.cnbr.as<int>(), (R)sigma,
                                                                    static_cast<const cpx<R> *>(x), static_cast<cpx<R> *>(y),
                                                                    dform ? 1 : 0);
     MG_CHECK_LAUNCH();
