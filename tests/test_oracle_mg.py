@@ -116,3 +116,37 @@ def test_gmres_and_fgmres_reach_dense_solution(setup4):
     # GMRES with tol = 0 runs exactly maxiter Arnoldi steps
     _, info = krylov.gmres(lambda v: op.Q_sigma(v, sigma), b, tol=0.0, restart=5, maxiter=7)
     assert info["iters"] == 7
+
+
+def test_deflated_preconditioner_solves_the_deflation_space_exactly(setup4):
+    """The fine-grid deflation of the eigensolver's shifted solves:
+    z = Z E^-1 Z^dag r + B (r - (Q - sigma) Z E^-1 Z^dag r), E = Z^dag (Q - sigma) Z.
+    For r = (Q - sigma) Z c the residual handed to B vanishes and z = Z c
+    exactly, for any Z and any B; for r orthogonal to Z the first term vanishes
+    and B sees r - (Q - sigma) Z E^-1 Z^dag r = r."""
+    from oracle import rqi
+    op, W, P, Dmat, Pmat = setup4
+    sigma = 0.07
+    Z = synth.gaussian_vectors(DIMS, 3, 5)
+
+    class Spy:                       # stands in for the two-grid method B
+        def __call__(self, r, s):
+            self.seen = r.copy()
+            return 2.0 * r
+
+    B = Spy()
+    M = rqi.deflated_preconditioner(op, Z, B, sigma)
+    coeff = np.array([0.3 - 0.2j, -1.1 + 0.5j, 0.7j])
+    zc = np.tensordot(coeff, Z, axes=1)
+    r = op.Q_sigma(zc, sigma)
+    out = M(r)
+    assert np.abs(B.seen).max() < 1e-12 * np.abs(r).max()
+    assert np.abs(out - zc).max() < 1e-12 * np.abs(zc).max()
+    # r orthogonal to span(Z): no deflation component, B gets r itself
+    Zf = Z.reshape(3, -1)
+    q, _ = np.linalg.qr(Zf.T)
+    r2 = synth.gaussian_vectors(DIMS, 1, 6)[0].ravel()
+    r2 = (r2 - q @ (q.conj().T @ r2)).reshape(zc.shape)
+    out2 = M(r2)
+    assert np.abs(B.seen - r2).max() < 1e-12 * np.abs(r2).max()
+    assert np.abs(out2 - 2.0 * r2).max() < 1e-12 * np.abs(r2).max()
