@@ -360,7 +360,7 @@ DEFAULT_PARAMS = dict(
     coarse_deflate=True,
     ritz_each_sweep=True,
     shift_floor=1e-6,
-    guard_maxiter=8,
+    guard_maxiter=4,
     ritz_keep=1e-6,
     fine_deflate=True,
     fine_deflate_radius=-1.0,

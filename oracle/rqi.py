@@ -158,7 +158,7 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
             # solvable by a single precision preconditioner)
             sigma = lam[i] * max(1.0 - max(res[i], p.get("shift_floor", 0.0)), 0.0)
             guard = ritz_each_sweep and i >= n_want
-            maxit = min(p.get("guard_maxiter", 8), p["outer_maxiter"]) if guard else p["outer_maxiter"]
+            maxit = min(p.get("guard_maxiter", 4), p["outer_maxiter"]) if guard else p["outer_maxiter"]
             # inexact solve: the new vector's eigen-residual is about tau |lambda - sigma|
             dls = abs(lam[i] - sigma)
             tau = p["solve_tol"] if (guard or dls == 0) else min(p["solve_tol"], max(0.1 * eps / dls, 1e-12))

@@ -106,7 +106,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->coarse_deflate = 1;
     p->ritz_each_sweep = 1;
     p->shift_floor = 1e-6;
-    p->guard_maxiter = 8;
+    p->guard_maxiter = 4;
     p->ritz_keep = 1e-6;
     p->fine_deflate = 1;
     p->fine_deflate_radius = -1.0;
