@@ -7,11 +7,14 @@ One step = the whole hot path on one synthetic gauge field already in device
 memory: gauge packing and the clover term, the multigrid setup (test vectors,
 P, coarse operator) and Algorithm 1 for the 20 lowest pairs.  `value` is the
 device time per step (lower is better); `e2e` repeats the step through the
-public C ABI from pinned host memory, copying the eigenvectors back.
+public C ABI from pinned host memory, copying the eigenvectors back.  The line
+also carries the 20 lowest pairs of the 32^3 x 64 field (one step, after the
+timed region), the stencil microbenchmark and the FP64 / FP32 FMA roofs.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --profile-case eig16|stencil32      (small cases for ncu)
 
---impl reference times the FP64 CPU oracle instead (see cpu_baseline()).
+--impl reference times the FP64 CPU oracle instead (see oracle_baseline()).
 N > 1 runs N independent replicas, one per rank (the path does not shard).
 """
 from __future__ import annotations
@@ -34,7 +37,7 @@ WORKLOAD = dict(
              "20 lowest eigenpairs of Q to resid 1e-10; 2-level MG (4^4 aggregates, 20 test vectors, SAP 4^4)",
     dims=[16, 16, 16, 32], eps=0.2, seed=1002, csw=1.9, n_eig=20, tol=1e-10,
 )
-COUNTS_FILE = os.path.join(ROOT, "bench_counts.json")
+ORACLE_WORK = os.path.join(ROOT, "tests", "golden", "oracle_work_8x8x8x16.json")
 # library timer classes that are one kernel each (the BLAS classes are several)
 SINGLE_KERNEL_CLASSES = ("coarse_gmres", "stencil_f64", "stencil_f32", "sap_f32", "sap_f64", "restrict", "prolong",
                          "coarse_apply", "coarse_build", "interp_build")
@@ -42,16 +45,20 @@ SINGLE_KERNEL_CLASSES = ("coarse_gmres", "stencil_f64", "stencil_f32", "sap_f32"
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where none was taken
 DRAM_BYTES_PER_LAUNCH = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:coarse_gmres -s 20 -c 3 on
-    # `python -m paper_1509_06865_gb300.profile_case --case eig16` (same 16^3x32 coarse grid): 66.0 MB read +
+    # `python bench.py --profile-case eig16` (same 16^3x32 coarse grid): 66.0 MB read +
     # 0.17 MB written per launch, whatever the number of GMRES steps (the coarse operator is read from DRAM once per
     # solve and then served by L2)
     "coarse_gmres": 66.17e6,
 }
 
 
-def load_m0() -> float:
+def workload(name: str) -> dict:
     with open(os.path.join(ROOT, "workloads.json")) as f:
-        m0 = json.load(f)["bench_16x16x16x32"]["m0"]
+        return json.load(f)[name]
+
+
+def load_m0() -> float:
+    m0 = workload("bench_16x16x16x32")["m0"]
     if m0 is None:
         raise RuntimeError("workloads.json: m0 of the 16^3x32 workload not tuned yet")
     return float(m0)
@@ -148,9 +155,11 @@ def max_over_ranks(dist, x: float, device):
 # GPU arm
 
 
-def stencil_microbench(ctx, dims, flush, peak_hbm, n=40):
+def stencil_microbench(ctx, dims, flush, peak_hbm, n=40, nrhs=0):
     """Q - sigma on device buffers, one launch per timed interval, L2 flushed
-    before each launch; CUDA events on the context's own stream."""
+    before each launch; CUDA events on the context's own stream.  With nrhs > 0
+    also the FP32 stencil on nrhs fields in one launch (links and clover read
+    once for all of them)."""
     import numpy as np
     import torch
 
@@ -160,6 +169,22 @@ def stencil_microbench(ctx, dims, flush, peak_hbm, n=40):
     V = int(np.prod(dims))
     s = torch.cuda.ExternalStream(ctx.stream())
     x_host = synth.gaussian_vectors(tuple(dims), 1, 77)
+
+    def timeit(launch):
+        for _ in range(3):
+            launch()
+        times = []
+        for _ in range(n):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            launch()
+            e1.record(s)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return statistics.median(times)
+
     out = {}
     # algorithmic bytes per site: x, y (12 complex each), 4 links (two rows in
     # FP32, full in FP64), clover (72 reals)
@@ -168,22 +193,20 @@ def stencil_microbench(ctx, dims, flush, peak_hbm, n=40):
         x = ctx.alloc_dev(nbytes)
         y = ctx.alloc_dev(nbytes)
         ctx.pack_spinors(x_host, x, prec)
-        for _ in range(3):
-            ctx.apply_dev(x, y, 1e-3, OP_Q, prec)
-        times = []
-        for _ in range(n):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            ctx.apply_dev(x, y, 1e-3, OP_Q, prec)
-            e1.record(s)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        ms = statistics.median(times)
+        ms = timeit(lambda: ctx.apply_dev(x, y, 1e-3, OP_Q, prec))
         gbs = per_site * V / (ms * 1e-3) / 1e9
         out[name] = dict(ms=ms, gbs=gbs, frac_hbm=gbs / peak_hbm, bytes_per_site=per_site,
                          gflops=1872.0 * V / (ms * 1e-3) / 1e9)
+    if nrhs > 0:
+        nbytes = V * 12 * 8
+        x = ctx.alloc_dev(nbytes * nrhs)
+        y = ctx.alloc_dev(nbytes * nrhs)
+        ctx.pack_spinors(np.repeat(x_host, nrhs, axis=0), x, PREC_F32)
+        ms = timeit(lambda: ctx.apply_dev_nrhs(x, y, nrhs, 1e-3, OP_Q, PREC_F32))
+        per_site = nrhs * (96 + 96) + 192 + 288
+        gbs = per_site * V / (ms * 1e-3) / 1e9
+        out[f"f32_nrhs{nrhs}"] = dict(ms=ms, ms_per_rhs=ms / nrhs, gbs=gbs, frac_hbm=gbs / peak_hbm,
+                                      bytes_per_site=per_site)
     return out
 
 
@@ -192,7 +215,7 @@ def run_gpu(args):
     import torch
 
     import synth
-    from paper_1509_06865_gb300 import FP64, MIXED, Context
+    from paper_1509_06865_gb300 import FP64, MIXED, PREC_F32, PREC_F64, Context
 
     rank, ws, local, dist = dist_init()
     torch.cuda.set_device(local)
@@ -233,6 +256,8 @@ def run_gpu(args):
 
     ctx = make_ctx(MIXED)
     ctx.load_gauge_dev(U_dev.data_ptr())
+    alu = dict(fp64_tflops=ctx.fma_peak(PREC_F64) / 1e12, fp32_tflops=ctx.fma_peak(PREC_F32) / 1e12,
+               how="own kernel: 8 independent FMA chains per thread on every SM, best of 5 launches, CUDA events")
     sten = stencil_microbench(ctx, dims, flush, peaks()["hbm"])
     # the same stencil on the 32^3 x 64 lattice of the larger workloads (unit links:
     # the stencil's memory traffic does not depend on the link values)
@@ -240,8 +265,12 @@ def run_gpu(args):
     ctxb = Context(big, device=local)
     ctxb.set_params(m0=m0, csw=w["csw"], n_tv=20, precision=MIXED)
     ctxb.load_gauge(synth.unit_gauge(big))
-    sten_big = stencil_microbench(ctxb, big, flush, peaks()["hbm"], n=20)
+    sten_big = stencil_microbench(ctxb, big, flush, peaks()["hbm"], n=20, nrhs=12)
     ctxb.close()
+    for k in ("f32", "f64"):
+        for sd in (sten, sten_big):
+            sd[k]["frac_fp64_fma_peak" if k == "f64" else "frac_fp32_fma_peak"] = \
+                sd[k]["gflops"] / 1e3 / (alu["fp64_tflops"] if k == "f64" else alu["fp32_tflops"])
     # the last warm-up step records every kernel class (the per-class breakdown);
     # the timed steps record events for the dominant single kernel only
     for i in range(args.warmup):
@@ -287,14 +316,18 @@ def run_gpu(args):
                     sweeps=st64["sweeps"], outer_iters=st64["outer_iters"],
                     max_abs_diff_vs_mixed=float(np.max(np.abs(np.asarray(lam) - np.asarray(lam64)))))
 
+    # the 20 lowest pairs of the 32^3 x 64 field (one step each, after the timed region)
+    north = None if args.no_north_star else north_star(args, flush, local)
+    # like for like: the GPU eigensolve of the 8^3 x 16 field on which the oracle's
+    # complete eigensolve was timed
+    small = small_field(flush, local)
+
     if rank != 0:
         return
     pk = peaks()
     # the dominant single kernel, its algorithmic bytes over its event-timed
     # duration inside the timed region
     achieved = kt_top["bytes"] / (kt_top["ms"] / 1e3) / 1e9 if kt_top["ms"] > 0 else None
-    with open(COUNTS_FILE + ".new", "w") as f:
-        json.dump(dict(workload=w["workload"], steps=1, kernels=kt, stats=st), f, indent=1)
     value = t_mixed / (args.steps * ws)
     line = dict(
         metric=METRIC, value=value, unit="s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
@@ -307,6 +340,9 @@ def run_gpu(args):
         result=dict(lambda_min=float(lam[0]), lambda_max=float(lam[-1]), max_resid=float(max(res)),
                     sweeps=st["sweeps"], solves=st["solves"], outer_iters=st["outer_iters"],
                     mg_cycles=st["mg_cycles"], coarse_iters=st["coarse_iters"]),
+        north_star_32x32x32x64=north,
+        like_for_like_8x8x8x16=small,
+        alu_peaks=alu,
         stencil=dict(sten, l2="flushed before every launch", lattice=w["dims"],
                      lattice_32x32x32x64=sten_big),
         roofline=dict(bound="hbm", kernel=top, achieved=achieved, peak=pk["hbm"], unit="GB/s",
@@ -324,137 +360,244 @@ def run_gpu(args):
         kernels_note="per-class device time of one step (the last warm-up step, every class timed)",
     )
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_subprocess(kt_counts=kt, stats=st, steps=1)   # kt covers one step
+        line["cpu_baseline"] = oracle_baseline_subprocess()
     print(json.dumps(line), flush=True)
+
+
+def north_star(args, flush, device):
+    """The 20 lowest pairs of Q on the 32^3 x 64 field to 1e-10 (mixed, and FP64
+    with --north-star-fp64), one step each, CUDA events around the step."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1509_06865_gb300 import FP64, MIXED, Context
+
+    cfg = workload("north_32x32x32x64")
+    if cfg["m0"] is None:
+        return dict(skipped="m0 of the 32^3x64 workload not tuned")
+    dims = tuple(cfg["dims"])
+    U = synth.gauge_field(dims, cfg["eps"], cfg["seed"])
+    U_dev = torch.from_numpy(U.view(np.float64).reshape(-1)).to(torch.device("cuda", device))
+    out = dict(workload=f"32^3x64 Wilson-clover, links exp(i {cfg['eps']} H), c_sw={cfg['csw']}, m0={cfg['m0']}; "
+                        f"{cfg['n_eig']} lowest eigenpairs of Q to resid {cfg['tol']}",
+               dims=cfg["dims"], m0=cfg["m0"], n_eig=cfg["n_eig"], tol=cfg["tol"])
+    for prec, name in ((MIXED, "mixed"), (FP64, "fp64")):
+        if prec == FP64 and not args.north_star_fp64:
+            continue
+        ctx = Context(dims, device=device)
+        ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
+                       sap_block=cfg["sap_block"], precision=prec)
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.load_gauge_dev(U_dev.data_ptr())
+        st0 = ctx.setup(cfg["seed"])
+        lam, _, res, st = ctx.eigensolve(cfg["n_eig"], cfg["tol"], want_vectors=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.close()
+        out[name] = dict(value=e0.elapsed_time(e1) / 1e3, unit="s", setup_s=st0["seconds"], eig_s=st["seconds"],
+                         converged=st["converged"], max_resid=float(max(res)), lambda_min=float(lam[0]),
+                         lambda_max=float(lam[-1]), sweeps=st["sweeps"], solves=st["solves"],
+                         outer_iters=st["outer_iters"], coarse_iters=st["coarse_iters"])
+    del U_dev
+    return out
+
+
+def small_field(flush, device):
+    """The 20 lowest pairs of the 8^3 x 16 field (mixed), the field of the oracle's
+    complete timed eigensolve (tests/golden/oracle_work_8x8x8x16.json)."""
+    import torch
+
+    import synth
+    from paper_1509_06865_gb300 import MIXED, Context
+
+    cfg = workload("check_8x8x8x16")
+    dims = tuple(cfg["dims"])
+    U = synth.gauge_field(dims, cfg["eps"], cfg["seed"])
+    ctx = Context(dims, device=device)
+    ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
+                   sap_block=cfg["sap_block"], precision=MIXED)
+    flush.fill_(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.load_gauge(U)
+    ctx.setup(cfg["seed"])
+    lam, _, res, st = ctx.eigensolve(cfg["n_eig"], cfg["tol"], want_vectors=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.close()
+    out = dict(gpu_s=e0.elapsed_time(e1) / 1e3, max_resid=float(max(res)), converged=st["converged"])
+    if os.path.exists(ORACLE_WORK):
+        with open(ORACLE_WORK) as f:
+            ow = json.load(f)
+        out.update(oracle_s=ow["wall_s"], oracle_cores=ow["host_cores_used"],
+                   oracle_host="the container that ran tests/golden/make_golden.py (x86-64), not the GPU box",
+                   oracle_over_gpu=ow["wall_s"] / out["gpu_s"])
+    return out
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and --impl reference)
 
 
-def cpu_baseline_subprocess(kt_counts=None, stats=None, steps=1):
-    """Run the oracle sample in a fresh single-threaded process."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    payload = json.dumps(dict(kernels=kt_counts, stats=stats, steps=steps))
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample"], input=payload,
-                       capture_output=True, text=True, env=env, timeout=900)
+def oracle_prices():
+    """Live oracle time of every operation the oracle's eigensolve performs, on
+    the 16^3 x 32 benchmark field (the coarse-operator build on the 8^3 x 16
+    field, scaled by the volume ratio: its work is per site)."""
+    import numpy as np
+
+    import synth
+    from oracle import dirac, mg
+
+    w = WORKLOAD
+    dims = tuple(w["dims"])
+    U = synth.gauge_field(dims, w["eps"], w["seed"])
+    t = {}
+
+    def clock(name, fn, reps=1):
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        t[name] = (time.perf_counter() - t0) / reps
+        return r
+
+    op = clock("clover", lambda: dirac.WilsonClover(U, load_m0(), w["csw"]))
+    x, y = synth.gaussian_vectors(dims, 2, 1)
+    clock("fine_D", lambda: op.D(x))
+    clock("fine_vdot_axpy", lambda: y + complex(np.vdot(x, y)) * x, reps=4)
+    sap = mg.SAP(op, (4, 4, 4, 4))
+    clock("sap_cycle", lambda: sap.smooth(y, x, 1e-3, 1, 4))
+    Wt = synth.uniform_vectors(dims, 20, 5)
+    P = clock("interp_build", lambda: mg.Interpolation(Wt, (4, 4, 4, 4)))
+    rc = clock("restrict", lambda: P.restrict(x))
+    clock("prolong", lambda: P.prolong(rc))
+    C = mg.CoarseOperator(np.zeros((9, P.nagg, 40, 40), dtype=np.complex128), P.cdims, 20)
+    clock("coarse_apply", lambda: C.apply(rc, 1e-3), reps=4)
+    small = (8, 8, 8, 16)
+    Us = synth.gauge_field(small, w["eps"], w["seed"])
+    ops = dirac.WilsonClover(Us, load_m0(), w["csw"])
+    Ps = mg.Interpolation(synth.uniform_vectors(small, 20, 5), (4, 4, 4, 4))
+    clock("coarse_build_8x8x8x16", lambda: mg.coarse_operator(ops, Ps))
+    t["coarse_build"] = t["coarse_build_8x8x8x16"] * int(np.prod(dims)) / int(np.prod(small))
+    # one SAP cycle applies D_sigma ten times (residual + 4 MR steps, two colours);
+    # those are counted with the stencil applications
+    t["sap_cycle_rest"] = max(0.0, t["sap_cycle"] - 10 * t["fine_D"])
+    return t
+
+
+def oracle_baseline():
+    """The oracle's own operation counts of a complete 20-pair eigensolve (the
+    8^3 x 16 field of the same generator, run to 1e-10 by
+    tests/golden/make_golden.py, which calls only oracle/), each priced by its
+    live oracle time on the 16^3 x 32 field.  The counts of a multigrid
+    eigensolve hardly depend on the volume (the premise of the method), the
+    price of each operation grows with it.  Returns the s per 20 eigenpairs and
+    how it was obtained; `cores` is the CPU time of the sample over its wall
+    time (numpy's element-wise kernels run on one core)."""
+    c0 = time.process_time()
+    t0 = time.perf_counter()
+    price = oracle_prices()
+    wall = time.perf_counter() - t0
+    cores = (time.process_time() - c0) / wall
+    with open(ORACLE_WORK) as f:
+        work = json.load(f)
+    n = work["counts"]
+    parts = dict(
+        stencil=n["fine_D_vectors"] * price["fine_D"],
+        sap_rest=n["sap_cycles"] * price["sap_cycle_rest"],
+        coarse_build=n["coarse_builds"] * price["coarse_build"],
+        interp_build=n["interp_builds"] * price["interp_build"],
+        restrict=n["restricts"] * price["restrict"],
+        prolong=n["prolongs"] * price["prolong"],
+        coarse_apply=n["coarse_applies"] * price["coarse_apply"],
+        fine_blas=n["fine_vdots"] * price["fine_vdot_axpy"],
+        clover=price["clover"],
+    )
+    return dict(value=sum(parts.values()), unit="s", cores=round(cores, 2), nproc=os.cpu_count(), kind="oracle",
+                sample="live FP64 oracle timings on the 16^3x32 field of one of each operation (Wilson-clover D, "
+                       "an SAP cycle, P from 20 test vectors, restriction, prolongation, a coarse apply, a fine "
+                       "vdot+axpy, the clover term; the coarse-operator build on the 8^3x16 field scaled by volume) "
+                       "x the operation counts of the oracle's own complete 20-pair eigensolve of the 8^3x16 field "
+                       f"({work['wall_s']:.0f} s wall there, tests/golden/oracle_work_8x8x8x16.json)",
+                sample_seconds=wall, parts_s=parts, prices_s=price, counts=n)
+
+
+def oracle_baseline_subprocess():
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample"], capture_output=True,
+                       text=True, timeout=1800)
     if r.returncode != 0:
         return dict(kind="oracle", error=r.stderr[-500:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_sample(counts: dict | None):
-    """Per-operation oracle times at 16^3x32, combined with the method's operation
-    counts per step (kernel launches by class of one GPU step; they are work
-    units of the algorithm on this workload, not results)."""
-    import numpy as np
-
-    import synth
-    from oracle import dirac, krylov, mg
-
-    w = WORKLOAD
-    dims = tuple(w["dims"])
-    t_all = time.perf_counter()
-    U = synth.gauge_field(dims, w["eps"], w["seed"])
-    t = time.perf_counter()
-    op = dirac.WilsonClover(U, load_m0(), w["csw"])
-    t_clover = time.perf_counter() - t
-    x = synth.gaussian_vectors(dims, 1, 1)[0]
-    t = time.perf_counter()
-    y = op.Q_sigma(x, 1e-3)
-    t_stencil = time.perf_counter() - t
-    Wt = synth.uniform_vectors(dims, 20, 5)
-    t = time.perf_counter()
-    P = mg.Interpolation(Wt, (4, 4, 4, 4))
-    t_interp = time.perf_counter() - t
-    t = time.perf_counter()
-    rc = P.restrict(x)
-    t_restrict = time.perf_counter() - t
-    t = time.perf_counter()
-    P.prolong(rc)
-    t_prolong = time.perf_counter() - t
-    # coarse operator: two of its 40 columns, scaled
-    t = time.perf_counter()
-    for c, j in ((0, 0), (1, 0)):
-        wv = P.column(c, j)
-        part = dirac.apply_local(op.A, op.m0, wv)
-        for mu in range(4):
-            part = part + dirac.hop_forward(op.U, wv, mu, op.bc) + dirac.hop_backward(op.U, wv, mu, op.bc)
-            P.restrict(part)
-            P.restrict(part)
-        P.restrict(part)
-    t_coarse_build = (time.perf_counter() - t) * 20
-    Dc = np.zeros((9, P.nagg, 40, 40), dtype=np.complex128)
-    C = mg.CoarseOperator(Dc, P.cdims, 20)
-    t = time.perf_counter()
-    C.apply(rc, 1e-3)
-    t_capply = time.perf_counter() - t
-    sap = mg.SAP(op, (4, 4, 4, 4))
-    t = time.perf_counter()
-    r = x - op.D_sigma(x, 1e-3)
-    sap.block_mr(r, 0, 1e-3, 4)
-    t_sap = time.perf_counter() - t          # one colour = one sweep
-    t = time.perf_counter()
-    for _ in range(4):
-        np.vdot(x, y)
-        y = y + 0.5 * x
-    t_blas = (time.perf_counter() - t) / 8
-    per_op = dict(stencil_f64=t_stencil, stencil_f32=t_stencil, sap_f64=t_sap, sap_f32=t_sap,
-                  restrict=t_restrict, prolong=t_prolong, coarse_apply=t_capply, coarse_build=t_coarse_build,
-                  interp_build=t_interp, blas_f64=t_blas * 3, blas_low=t_blas * 3 * 40 / V_ratio(),
-                  other=t_clover)
-    if counts and counts.get("kernels"):
-        kt = counts["kernels"]
-        steps = max(1, int(counts.get("steps", 1)))
-        est = sum(per_op.get(k, 0.0) * v["launches"] / steps for k, v in kt.items())
-        how = "per-op oracle times x the method's per-step launch counts"
-    else:
-        est = None
-        how = "per-op oracle times only (no launch counts)"
-    return dict(value=est, unit="s", cores=1, kind="oracle",
-                sample=f"oracle FP64 at 16^3x32: 1 stencil, 1 SAP sweep, P build, restrict, prolong, "
-                       f"2 of 40 coarse-operator columns (x20), 1 coarse apply, BLAS-1, clover; {how}",
-                sample_seconds=time.perf_counter() - t_all, per_op_s=per_op)
-
-
-def V_ratio():
-    # BLAS-1 on coarse vectors (512 x 40 complex) vs fine vectors (131072 x 12)
-    return 131072 * 12 / (512 * 40)
-
-
 def run_reference(args):
+    """The oracle arm: every warm-up and timed step is a complete oracle_baseline()
+    measurement on this host; value = their median."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    counts = None
-    if os.path.exists(COUNTS_FILE):
-        with open(COUNTS_FILE) as f:
-            counts = json.load(f)
-    vals = []
     for _ in range(args.warmup):
-        pass
+        oracle_baseline()
     t0 = time.perf_counter()
-    for _ in range(max(1, args.steps)):
-        r = cpu_baseline_subprocess_from(counts)
-        vals.append(r.get("value"))
+    runs = [oracle_baseline() for _ in range(max(1, args.steps))]
     elapsed = time.perf_counter() - t0
-    v = statistics.median([x for x in vals if x is not None]) if any(x is not None for x in vals) else None
+    v = statistics.median(r["value"] for r in runs)
+    last = runs[-1]
     line = dict(impl="reference", metric=METRIC, value=v, unit="s", n_gpus=1, steps=args.steps,
-                warmup=args.warmup, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
-                data="synthetic", config=dict(workload=WORKLOAD["workload"], dims=WORKLOAD["dims"]),
-                cpu_baseline=dict(r, value=v),
+                warmup=args.warmup, ms_per_step=1e3 * elapsed / max(1, args.steps), higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD["workload"], dims=WORKLOAD["dims"], m0=load_m0(),
+                            n_eig=WORKLOAD["n_eig"], tol=WORKLOAD["tol"]),
+                cpu_baseline=dict(last, value=v, values=[r["value"] for r in runs]),
                 e2e=dict(value=v, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
                 wall_s=elapsed)
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_subprocess_from(counts):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample"],
-                       input=json.dumps(counts or {}), capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        return dict(kind="oracle", error=r.stderr[-500:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+# ---------------------------------------------------------------------------
+# small self-terminating cases for ncu (one GPU, a few GB)
+
+
+def profile_case(case: str):
+    """stencil32: five FP32 applications of Q - sigma on a 32^3 x 64 lattice with
+    unit links (the stencil's memory traffic does not depend on the link values),
+    about 4 GB of device memory.
+
+    eig16: the 16^3 x 32 benchmark field, multigrid setup with one refinement
+    pass, then one sweep of Algorithm 1 on 3 vectors without guards to
+    eigen-residual 1e-3: every kernel of the hot path a few hundred times at the
+    benchmark's lattice size, in a few seconds and a few GB of device memory."""
+    import synth
+    from paper_1509_06865_gb300 import MIXED, OP_Q, PREC_F32, Context
+
+    if case == "stencil32":
+        dims = (32, 32, 32, 64)
+        ctx = Context(dims)
+        ctx.set_params(m0=-0.05, csw=1.9, n_tv=20, precision=MIXED)
+        ctx.load_gauge(synth.unit_gauge(dims))
+        nbytes = 32 * 32 * 32 * 64 * 12 * 8
+        x, y = ctx.alloc_dev(nbytes), ctx.alloc_dev(nbytes)
+        ctx.pack_spinors(synth.gaussian_vectors(dims, 1, 77)[0], x, PREC_F32)
+        for _ in range(5):
+            ctx.apply_dev(x, y, 1e-3, OP_Q, PREC_F32)
+        ctx.close()
+        print("profile case", case, "ok")
+        return
+    cfg = workload("bench_16x16x16x32")
+    dims = tuple(cfg["dims"])
+    U = synth.gauge_field(dims, cfg["eps"], cfg["seed"])
+    ctx = Context(dims)
+    ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], n_tv=cfg["n_tv"], precision=MIXED, setup_iters=1,
+                   max_sweeps=1, n_guard=0)
+    ctx.load_gauge(U)
+    ctx.setup(cfg["seed"])
+    _, _, _, st = ctx.eigensolve(3, 1e-3, want_vectors=False)
+    ctx.close()
+    print("profile case", case, st)
 
 
 def main():
@@ -465,12 +608,16 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-north-star", action="store_true", help="skip the 32^3x64 eigensolve")
+    ap.add_argument("--north-star-fp64", action="store_true", help="also the all-FP64 32^3x64 eigensolve")
+    ap.add_argument("--profile-case", choices=["eig16", "stencil32"])
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
-        payload = sys.stdin.read()
-        counts = json.loads(payload) if payload.strip() else None
-        print(json.dumps(oracle_sample(counts)))
+        print(json.dumps(oracle_baseline()))
+        return
+    if args.profile_case:
+        profile_case(args.profile_case)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -62,6 +62,9 @@ extern "C" {
 /* smoother of the two-grid cycle (Sec. 2) */
 #define MGEIG_SAP 0    /* SAP on D_sigma with right-hand side gamma5 r            */
 #define MGEIG_GMRES 1  /* restarted GMRES(k) on Q - sigma                         */
+#define MGEIG_LEARNED 2 /* the learned smoother (mgeig_net_*) on the residual after
+                           the coarse correction; MGEIG_MIXED only; the setup and
+                           the start vectors of Algorithm 1 still smooth with SAP */
 
 /* operator selector of mgeig_apply */
 #define MGEIG_OP_Q 0   /* y = (Q - sigma) x                                       */
@@ -70,6 +73,13 @@ extern "C" {
 /* arithmetic of mgeig_apply */
 #define MGEIG_PREC_F64 0
 #define MGEIG_PREC_F32 1
+
+/* storage of the coarse operator's links in the mixed-precision preconditioner
+ * (spec extension of the Sec. 2.2 precision split: the coarse operator in
+ * 16 bits with one FP32 scale per 2N_tv x 2N_tv link block, FP32 arithmetic) */
+#define MGEIG_LINKS_LEVEL 0   /* the level precision (FP32 in MGEIG_MIXED)            */
+#define MGEIG_LINKS_BF16 1    /* bfloat16 entries / per-link FP32 scale               */
+#define MGEIG_LINKS_F16 2     /* IEEE half entries / per-link FP32 scale              */
 
 typedef struct mgeig_ctx mgeig_ctx;
 
@@ -121,6 +131,20 @@ typedef struct mgeig_params {
     double fine_deflate_radius;  /* Z of the solve for v_i: v_i and the iterated
                              vectors whose Rayleigh quotient lies within this
                              distance of sigma (< 0: all iterated vectors)      */
+    int adaptive_tol;     /* 1: the shifted solve of v_i runs to relative
+                             residual min(solve_tol, 0.1 tol / |lambda_i - sigma|)
+                             (the new eigen-residual is about that times
+                             |lambda_i - sigma|); 0: solve_tol for every solve   */
+    int ritz_start;       /* 1: Algorithm 1 starts from the Ritz vectors of Q in
+                             the span of the setup's test vectors (same span,
+                             same P), ordered by |theta|; 0: from the test
+                             vectors in the order the setup leaves them          */
+    int coarse_links;     /* MGEIG_LINKS_*: how the coarse operator is stored and
+                             read by the coarse solver and coarse applies (16-bit
+                             links only with MGEIG_MIXED)                        */
+    double barrier_timeout;   /* seconds (of SM clock) a block of the persistent
+                             coarse solver waits at a grid barrier before it gives
+                             up, raises MGEIG_ETIMEOUT and returns              */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */
@@ -160,6 +184,20 @@ int mgeig_load_gauge(mgeig_ctx *ctx, const double *U);
  * host layout, complex128), e.g. a buffer allocated with mgeig_alloc_dev. */
 int mgeig_load_gauge_dev(mgeig_ctx *ctx, const void *U_dev);
 
+/* Replace the clover term of the operator (Sec. 2: D is the clover-improved
+ * Wilson operator) by a caller's A(x) = c_sw (i/4) sum_{mu nu} sigma_{mu nu} F_{mu nu}(x),
+ * e.g. one computed with another clover definition or improvement coefficient.
+ *   A   host complex128 [site][chirality 2][6][6], the layout of mgeig_get_clover
+ *       (c_sw included, the mass term 4 + m0 not), or NULL to go back to the
+ *       term the library builds from the gauge field.  Each 6x6 block must be
+ *       Hermitian: only the real diagonal and the upper triangle are read.
+ *       Copied; the caller keeps ownership.
+ * Needs a loaded gauge field (MGEIG_ENOTSETUP otherwise); the loaded term stays
+ * in use across mgeig_set_params (which re-adds the new mass) until the next
+ * mgeig_load_clover(ctx, NULL) or gauge load.  Drops an existing multigrid
+ * setup (the operator changed). */
+int mgeig_load_clover(mgeig_ctx *ctx, const double *A);
+
 /* Copy the clover term A(x) = c_sw (i/4) sum sigma F (without the mass term) to
  * host memory as complex128 [site][chirality 2][6][6]; row/col = 3*spin' + colour
  * with spin' = spin mod 2 inside the chirality block. */
@@ -167,7 +205,8 @@ int mgeig_get_clover(mgeig_ctx *ctx, double *A);
 
 /* y = (Q - sigma) x (op = MGEIG_OP_Q) or (D - sigma gamma5) x (MGEIG_OP_D) for
  * nrhs host spinors stored one after another, computed in FP64 or in FP32
- * (inputs rounded to FP32, result widened back).  Fine stencil, Sec. 2. */
+ * (inputs rounded to FP32, result widened back), all right-hand sides in one
+ * launch (mgeig_apply_dev_nrhs).  Fine stencil, Sec. 2. */
 int mgeig_apply(mgeig_ctx *ctx, double sigma, int op, int prec,
                 const double *x, double *y, int nrhs);
 
@@ -177,6 +216,15 @@ int mgeig_apply(mgeig_ctx *ctx, double sigma, int op, int prec,
  * context's stream, asynchronous.  For timing the stencil without copies. */
 int mgeig_apply_dev(mgeig_ctx *ctx, double sigma, int op, int prec,
                     const void *x, void *y);
+
+/* The stencil of mgeig_apply_dev on nrhs device fields at once: x and y each
+ * hold nrhs fields of the internal layout of precision prec stored back to back
+ * (field k at byte offset k * V * 12 * (16 for FP64, 8 for FP32)); x and y must
+ * not overlap (MGEIG_EINVAL).  One launch for all fields, so the links and the
+ * clover term are read from HBM once for all of them (the multi right-hand-side
+ * form of the fine stencil, Sec. 2, as used for many right-hand sides of Z2
+ * noise, Sec. 3, Eqs. 3.4-3.6).  Asynchronous on the context's stream. */
+int mgeig_apply_dev_nrhs(mgeig_ctx *ctx, double sigma, int op, int prec, const void *x, void *y, int nrhs);
 
 /* Device buffer of `bytes` bytes owned by the context (freed by destroy), e.g.
  * for mgeig_apply_dev operands.  *ptr = NULL on error. */
@@ -222,6 +270,18 @@ int mgeig_prolong(mgeig_ctx *ctx, const double *ec, double *e);
 /* y_c = (gamma5^c D_c - sigma) x_c = (Q_c - sigma) x_c (Eq. 2.6). */
 int mgeig_coarse_apply(mgeig_ctx *ctx, double sigma, const double *xc, double *yc);
 
+/* y_c = (Q_c - sigma) x_c for nrhs <= 16 host coarse vectors stored one after
+ * another (Eq. 2.6).  With MGEIG_MIXED and MGEIG_LINKS_BF16 one launch on the
+ * tensor cores (BF16 links with their per-link FP32 scale, right-hand sides
+ * rounded to BF16 after the scale is applied, FP32 accumulation); with the
+ * other link formats the CUDA-core coarse apply per right-hand side. */
+int mgeig_coarse_apply_nrhs(mgeig_ctx *ctx, double sigma, const double *xc, double *yc, int nrhs);
+
+/* The same on device memory, MGEIG_MIXED only: X and Y hold nrhs FP32 coarse
+ * vectors (complex64 [coarse site][2][n_tv] each) back to back, must not
+ * overlap (MGEIG_EINVAL).  Asynchronous on the context's stream. */
+int mgeig_coarse_apply_dev_nrhs(mgeig_ctx *ctx, double sigma, const void *X, void *Y, int nrhs);
+
 /* cycles SAP cycles (red then black blocks, sap_mr_iters MR steps per block)
  * for D_sigma z = b from z (both host spinors; z updated in place). */
 int mgeig_sap(mgeig_ctx *ctx, double sigma, const double *b, double *z, int cycles);
@@ -238,20 +298,28 @@ int mgeig_mg_cycle(mgeig_ctx *ctx, double sigma, const double *r, double *z);
  *   r, z   device spinors in the context's level precision and internal layout
  *          (MGEIG_PREC_F32 for MGEIG_MIXED, MGEIG_PREC_F64 for MGEIG_FP64, as
  *          mgeig_pack_spinors writes them); r is read, z is overwritten.  The
- *          caller owns both.
+ *          caller owns both; they must not overlap (MGEIG_EINVAL otherwise:
+ *          the prolongation writes z before the smoother reads r).
  * The result equals mgeig_mg_cycle's.  On success the call allocates nothing:
  * the coarse vectors and the coarse solver's scratch live in one static device
  * array of 16 MiB that every GPU loading this library holds until the process
- * exits.  Coarse grids needing more (about (coarse_restart + 4) x n_agg x
- * 2 n_tv complex values in the level precision, plus the solver's per-block
- * partial sums) return MGEIG_ESCRATCH; the 16^3 x 32 lattice with 4^4
- * aggregates and 20 test vectors fits in both precisions.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array, so calls
- * that overlap on the GPU race.  Needs the SAP smoother and kernel timing off
- * (MGEIG_EINVAL otherwise); the coarse-grid deflation data for sigma is
- * computed on the first call at a new sigma, as in mgeig_mg_cycle.  Returns
- * after the cycle has finished on the context's stream. */
+ * exits.  Coarse grids needing more return MGEIG_ESCRATCH: it holds three coarse
+ * vectors (n_agg x 2 n_tv complex values in the level precision each) plus the
+ * coarse solver's per-block partial sums, and, on coarse grids too large for the
+ * solver to keep its per-block vectors in shared memory, another
+ * (2 coarse_restart + 5) coarse vectors; the 16^3 x 32 lattice with 4^4
+ * aggregates and 20 test vectors fits in both precisions.  mgeig_create looks
+ * up the array's device address (cudaGetSymbolAddress, once per device), which
+ * also loads the code module that holds the array, so calls on a context made
+ * after mgeig_create allocate no device memory of the library's own.  (With
+ * CUDA's lazy loading the driver may still load a kernel's code the first time
+ * it runs; a caller that must exclude that makes one call ahead of time or sets
+ * CUDA_MODULE_LOADING=EAGER.)  All calls share the array, so calls that overlap
+ * on the GPU race.  Needs the SAP smoother and kernel timing off (MGEIG_EINVAL
+ * otherwise); the coarse-grid deflation data for sigma is computed on the first
+ * call at a new sigma, as in mgeig_mg_cycle.  The call synchronises the
+ * context's stream before it returns (it reads the coarse solver's status words
+ * back), so the cycle has finished when it returns. */
 int mgeig_mg_cycle_dev_noalloc(mgeig_ctx *ctx, double sigma, const void *r, void *z);
 
 /* Solve (Q - sigma) x = b with FP64 flexible GMRES preconditioned by the two-grid
@@ -299,6 +367,50 @@ int mgeig_get_stream(mgeig_ctx *ctx, void **stream);
  * calls, including mgeig_load_gauge*); *count is written on success.  The
  * paper has no counterpart: it lets a caller count the device work of a step. */
 int mgeig_get_launch_count(mgeig_ctx *ctx, long long *count);
+
+/* ---------------------------------------------------------------------------
+ * The learned smoother (the paper has none; spec extension of the
+ * smoother M of Eq. 2.3): a 3-layer 4D convolutional network (3^4 taps,
+ * 24 -> 32 -> 32 -> 24 real channels, no bias, GELU in its tanh form between
+ * the layers), applied as M(r) = ||r|| f(r / ||r||), trained on the GPU with the
+ * library's own tensor-core kernels on (residual, SAP correction) pairs that the
+ * two-grid method produces.  Weights: FP32 [layer 3][tap 81][out 32][in 32],
+ * tap = ((dt+1)*3 + (dz+1))*9 + (dy+1)*3 + (dx+1); unused channels zero.
+ * The lattice extents must be multiples of 4, 4, 4, 2 (MGEIG_EINVAL).
+ * -------------------------------------------------------------------------- */
+
+/* He-normal initialisation of the weights from `seed` (64-bit Mersenne twister,
+ * Box-Muller), standard deviation 0.5 sqrt(2 / (81 c_in)); resets Adam. */
+int mgeig_net_init(mgeig_ctx *ctx, uint64_t seed);
+
+/* Copy the FP32 master weights in (resets Adam) or out (layout above). */
+int mgeig_net_set_weights(mgeig_ctx *ctx, const float *W);
+int mgeig_net_get_weights(mgeig_ctx *ctx, float *W);
+
+/* `steps` Adam steps (learning rate lr) on `batch` fresh pairs each: random
+ * Philox vectors v (stream 0x5EED0004, key seed + step), the coarse correction
+ * x_c = P (Q_c)^-1 P^dag v, the residual r = v - Q x_c, the target e = the SAP
+ * correction of r (sap_cycles cycles on D e = gamma5 r from e = 0); loss
+ * 1/(2 batch) sum ||f(r/||r||) - e/||r||||^2.  losses[steps] (may be NULL)
+ * receives the loss of every step.  Needs mgeig_setup; MGEIG_MIXED only. */
+int mgeig_net_train(mgeig_ctx *ctx, int steps, int batch, double lr, uint64_t seed, double *losses);
+
+/* Loss and weight gradients (FP32, layout of the weights) for caller data: x and
+ * t are FP64 channel fields [batch][site][24] (channel 2k = Re, 2k+1 = Im of
+ * spin-colour component k), loss = 1/(2 batch) sum ||f(x) - t||^2.  For checking
+ * the GPU forward and backward kernels; weights as set. */
+int mgeig_net_loss_grads(mgeig_ctx *ctx, const double *x, const double *t, int batch, double *loss, float *G);
+
+/* e = M(r) = ||r|| f(r / ||r||) for one host spinor (computed from its FP32
+ * rounding, result widened to FP64). */
+int mgeig_net_apply(mgeig_ctx *ctx, const double *r, double *e);
+
+/* FMA throughput of the device in FP64 (prec = MGEIG_PREC_F64) or FP32
+ * (MGEIG_PREC_F32), in FLOP/s (2 per FMA), measured with the library's own
+ * kernel (independent FMA chains on every SM, best of `reps` launches timed with
+ * CUDA events on the context's stream).  The paper has no counterpart: it is the
+ * arithmetic roof of the kernels whose FP64 work, not memory, bounds them. */
+int mgeig_fma_peak(mgeig_ctx *ctx, int prec, int reps, double *flops);
 
 /* Name of a status code. */
 const char *mgeig_strerror(int status);

@@ -364,6 +364,8 @@ DEFAULT_PARAMS = dict(
     ritz_keep=1e-6,
     fine_deflate=True,
     fine_deflate_radius=-1.0,
+    adaptive_tol=True,
+    ritz_start=True,
     outer_restart=20,
     outer_maxiter=50,
     solve_tol=1e-2,

@@ -18,12 +18,19 @@ the N_eig pairs of smallest |lambda| are returned.  The guard vectors
 pair, the failure the paper describes after Algorithm 1, by spanning whole
 clusters of nearly equal eigenvalues.
 
+With ritz_start off the test vectors start Algorithm 1 in the setup's order;
+with adaptive_tol off every shifted solve runs to solve_tol.  With every
+addition off (ritz_start, adaptive_tol, ritz_each_sweep, fine_deflate,
+coarse_deflate, shift_floor = 0, n_guard = 0) this is Algorithm 1 in the
+paper's order.
+
 Algorithm 1, per sweep over the unconverged i:
     sigma   = lambda_i * max(1 - max(eps_i, floor), 0)     (damped shift; floor:
               shift_floor, so that |lambda - sigma| stays resolvable)
     v_i    <- (Q - sigma)^-1 v_i                           (FGMRES + two-grid, FP64, to
-              relative residual min(solve_tol, 0.1 eps / |lambda_i - sigma|): the
-              new vector's eigen-residual is about that tolerance times |lambda_i - sigma|;
+              relative residual min(solve_tol, 0.1 eps / |lambda_i - sigma|) with
+              adaptive_tol, else solve_tol: the new vector's eigen-residual is
+              about that tolerance times |lambda_i - sigma|;
               with fine_deflate the two-grid preconditioner is deflated by v_i and
               the iterated vectors whose Rayleigh quotient lies within
               fine_deflate_radius of sigma, see deflated_preconditioner)
@@ -161,7 +168,10 @@ def rqi(op: dirac.WilsonClover, V: np.ndarray, extra: np.ndarray, B: mg.TwoGrid,
             maxit = min(p.get("guard_maxiter", 4), p["outer_maxiter"]) if guard else p["outer_maxiter"]
             # inexact solve: the new vector's eigen-residual is about tau |lambda - sigma|
             dls = abs(lam[i] - sigma)
-            tau = p["solve_tol"] if (guard or dls == 0) else min(p["solve_tol"], max(0.1 * eps / dls, 1e-12))
+            if guard or dls == 0 or not p.get("adaptive_tol", True):
+                tau = p["solve_tol"]
+            else:
+                tau = min(p["solve_tol"], max(0.1 * eps / dls, 1e-12))
             if p.get("fine_deflate", False):
                 # z_i and the iterated vectors with Rayleigh quotient within the radius of sigma
                 rad = p.get("fine_deflate_radius", -1.0)
@@ -233,7 +243,8 @@ def eigensolve(op: dirac.WilsonClover, W0: np.ndarray, n_eig: int, eps: float, p
     n_run = n_eig + guard
     if n_run > ntv:
         W = np.concatenate([W, extra_start_vectors(op, B, W, n_run - ntv, seed, params)])
-    W, _ = ritz_rotate(op, W)
+    if params.get("ritz_start", True):
+        W, _ = ritz_rotate(op, W)
     extra = W[n_run:] if W.shape[0] > n_run else None
     lam, V, res, st = rqi(op, W[:n_run], extra, B, n_run, eps, params, max_sweeps, log, n_want=n_eig)
     return lam[:n_eig], V[:n_eig], res[:n_eig], st

@@ -17,9 +17,11 @@ LIB_PATH = os.path.join(_HERE, "libmgeig.so")
 
 OK, EINVAL, ENOTSETUP, ECUDA, ENOCONV, EBREAKDOWN, ENOMEM, ETIMEOUT, ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FP64, MIXED = 0, 1
-SAP, GMRES = 0, 1
+SAP, GMRES, LEARNED = 0, 1, 2
+NET_SHAPE = (3, 81, 32, 32)   # learned smoother weights [layer][tap][out][in]
 OP_Q, OP_D = 0, 1
 PREC_F64, PREC_F32 = 0, 1
+LINKS_LEVEL, LINKS_BF16, LINKS_F16 = 0, 1, 2
 
 
 class Params(C.Structure):
@@ -33,6 +35,8 @@ class Params(C.Structure):
         ("n_guard", C.c_int), ("coarse_deflate", C.c_int), ("ritz_each_sweep", C.c_int),
         ("shift_floor", C.c_double), ("guard_maxiter", C.c_int), ("ritz_keep", C.c_double),
         ("fine_deflate", C.c_int), ("fine_deflate_radius", C.c_double),
+        ("adaptive_tol", C.c_int), ("ritz_start", C.c_int), ("coarse_links", C.c_int),
+        ("barrier_timeout", C.c_double),
     ]
 
 
@@ -73,8 +77,10 @@ def load():
         "mgeig_load_gauge": (I, [P, P]),
         "mgeig_load_gauge_dev": (I, [P, P]),
         "mgeig_get_clover": (I, [P, P]),
+        "mgeig_load_clover": (I, [P, P]),
         "mgeig_apply": (I, [P, D, I, I, P, P, I]),
         "mgeig_apply_dev": (I, [P, D, I, I, P, P]),
+        "mgeig_apply_dev_nrhs": (I, [P, D, I, I, P, P, I]),
         "mgeig_alloc_dev": (I, [P, S, C.POINTER(P)]),
         "mgeig_pack_spinors": (I, [P, I, P, P, I]),
         "mgeig_unpack_spinors": (I, [P, I, P, P, I]),
@@ -86,6 +92,8 @@ def load():
         "mgeig_restrict": (I, [P, P, P]),
         "mgeig_prolong": (I, [P, P, P]),
         "mgeig_coarse_apply": (I, [P, D, P, P]),
+        "mgeig_coarse_apply_nrhs": (I, [P, D, P, P, I]),
+        "mgeig_coarse_apply_dev_nrhs": (I, [P, D, P, P, I]),
         "mgeig_sap": (I, [P, D, P, P, I]),
         "mgeig_mg_cycle": (I, [P, D, P, P]),
         "mgeig_solve": (I, [P, D, P, P, D, C.POINTER(Stats)]),
@@ -96,6 +104,13 @@ def load():
         "mgeig_get_stream": (I, [P, C.POINTER(P)]),
         "mgeig_get_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
         "mgeig_mg_cycle_dev_noalloc": (I, [P, D, P, P]),
+        "mgeig_fma_peak": (I, [P, I, I, C.POINTER(D)]),
+        "mgeig_net_init": (I, [P, C.c_uint64]),
+        "mgeig_net_set_weights": (I, [P, P]),
+        "mgeig_net_get_weights": (I, [P, P]),
+        "mgeig_net_train": (I, [P, I, I, D, C.c_uint64, P]),
+        "mgeig_net_loss_grads": (I, [P, P, P, I, C.POINTER(D), P]),
+        "mgeig_net_apply": (I, [P, P, P]),
         "mgeig_strerror": (C.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -180,6 +195,16 @@ class Context:
     def load_gauge_dev(self, U_dev_ptr: int):
         self._check("mgeig_load_gauge_dev", self.lib.mgeig_load_gauge_dev(self._h, C.c_void_p(U_dev_ptr)))
 
+    def load_clover(self, A=None):
+        """Use the clover term A ([site][2][6][6] complex128, no mass term) instead of
+        the one built from the gauge field; None goes back to the built one."""
+        if A is None:
+            self._check("mgeig_load_clover", self.lib.mgeig_load_clover(self._h, None))
+            return
+        A = _c128(A)
+        assert A.size == self.V * 72
+        self._check("mgeig_load_clover", self.lib.mgeig_load_clover(self._h, _ptr(A)))
+
     def get_clover(self):
         out = np.empty((self.V, 2, 6, 6), dtype=np.complex128)
         self._check("mgeig_get_clover", self.lib.mgeig_get_clover(self._h, _ptr(out)))
@@ -196,6 +221,11 @@ class Context:
     def apply_dev(self, x_ptr: int, y_ptr: int, sigma=0.0, op=OP_Q, prec=PREC_F64):
         self._check("mgeig_apply_dev", self.lib.mgeig_apply_dev(self._h, float(sigma), op, prec,
                                                                 C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+    def apply_dev_nrhs(self, x_ptr: int, y_ptr: int, nrhs: int, sigma=0.0, op=OP_Q, prec=PREC_F64):
+        self._check("mgeig_apply_dev_nrhs", self.lib.mgeig_apply_dev_nrhs(self._h, float(sigma), op, prec,
+                                                                          C.c_void_p(x_ptr), C.c_void_p(y_ptr),
+                                                                          int(nrhs)))
 
     def alloc_dev(self, nbytes: int) -> int:
         p = C.c_void_p()
@@ -258,6 +288,18 @@ class Context:
         self._check("mgeig_coarse_apply", self.lib.mgeig_coarse_apply(self._h, float(sigma), _ptr(xc), _ptr(yc)))
         return yc
 
+    def coarse_apply_nrhs(self, xc, sigma=0.0):
+        """(Q_c - sigma) on nrhs coarse vectors xc[nrhs, sites, 2, n_tv] in one call."""
+        xc = _c128(xc)
+        yc = np.empty_like(xc)
+        self._check("mgeig_coarse_apply_nrhs", self.lib.mgeig_coarse_apply_nrhs(self._h, float(sigma), _ptr(xc),
+                                                                                _ptr(yc), xc.shape[0]))
+        return yc
+
+    def coarse_apply_dev_nrhs(self, x_ptr: int, y_ptr: int, nrhs: int, sigma=0.0):
+        self._check("mgeig_coarse_apply_dev_nrhs", self.lib.mgeig_coarse_apply_dev_nrhs(
+            self._h, float(sigma), C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs)))
+
     def sap(self, b, z, sigma=0.0, cycles=1):
         b = _c128(b)
         z = _c128(z).copy()
@@ -301,6 +343,48 @@ class Context:
         s = C.c_void_p()
         self._check("mgeig_get_stream", self.lib.mgeig_get_stream(self._h, C.byref(s)))
         return s.value or 0
+
+    # ---- learned smoother ------------------------------------------------
+    def net_init(self, seed: int):
+        self._check("mgeig_net_init", self.lib.mgeig_net_init(self._h, C.c_uint64(seed)))
+
+    def net_set_weights(self, W):
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        assert W.shape == NET_SHAPE
+        self._check("mgeig_net_set_weights", self.lib.mgeig_net_set_weights(self._h, _ptr(W)))
+
+    def net_get_weights(self):
+        W = np.empty(NET_SHAPE, dtype=np.float32)
+        self._check("mgeig_net_get_weights", self.lib.mgeig_net_get_weights(self._h, _ptr(W)))
+        return W
+
+    def net_train(self, steps: int, batch: int, lr: float, seed: int):
+        losses = np.empty(steps)
+        self._check("mgeig_net_train", self.lib.mgeig_net_train(self._h, int(steps), int(batch), float(lr),
+                                                                C.c_uint64(seed), _ptr(losses)))
+        return losses
+
+    def net_loss_grads(self, x, t):
+        """x, t: FP64 channel fields [batch, T, Z, Y, X, 24] -> (loss, gradients [3, 81, 32, 32])."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        G = np.empty(NET_SHAPE, dtype=np.float32)
+        L = C.c_double()
+        self._check("mgeig_net_loss_grads", self.lib.mgeig_net_loss_grads(self._h, _ptr(x), _ptr(t), x.shape[0],
+                                                                          C.byref(L), _ptr(G)))
+        return L.value, G
+
+    def net_apply(self, r):
+        r = _c128(r)
+        e = np.empty_like(r)
+        self._check("mgeig_net_apply", self.lib.mgeig_net_apply(self._h, _ptr(r), _ptr(e)))
+        return e
+
+    def fma_peak(self, prec=PREC_F64, reps: int = 5) -> float:
+        """FMA throughput of the device in FLOP/s (FP64 or FP32), own kernel."""
+        f = C.c_double()
+        self._check("mgeig_fma_peak", self.lib.mgeig_fma_peak(self._h, prec, int(reps), C.byref(f)))
+        return f.value
 
     def launch_count(self) -> int:
         n = C.c_longlong()

@@ -55,9 +55,14 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (!(p.ritz_keep >= 0) || !std::isfinite(p.ritz_keep)) return MGEIG_EINVAL;
     if (p.fine_deflate != 0 && p.fine_deflate != 1) return MGEIG_EINVAL;
     if (!std::isfinite(p.fine_deflate_radius)) return MGEIG_EINVAL;
+    if ((p.adaptive_tol != 0 && p.adaptive_tol != 1) || (p.ritz_start != 0 && p.ritz_start != 1)) return MGEIG_EINVAL;
+    if (p.coarse_links < MGEIG_LINKS_LEVEL || p.coarse_links > MGEIG_LINKS_F16) return MGEIG_EINVAL;
+    if (p.coarse_links != MGEIG_LINKS_LEVEL && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
+    if (!(p.barrier_timeout > 0) || !(p.barrier_timeout <= 60)) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
-    if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES) return MGEIG_EINVAL;
+    if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES && p.smoother != MGEIG_LEARNED) return MGEIG_EINVAL;
+    if (p.smoother == MGEIG_LEARNED && (p.precision != MGEIG_MIXED || !net_supported(c))) return MGEIG_EINVAL;
     if (p.max_sweeps < 1 || p.n_guard < -1) return MGEIG_EINVAL;
     return MGEIG_OK;
 }
@@ -77,6 +82,13 @@ void internal_to_host(Ctx &c, const void *src, double *host) {
 }
 
 }  // namespace
+
+namespace mgeig {
+void refresh_clover(Ctx &c) {
+    if (c.clover_loaded) pack_clover(c, c.clov_user.as<double>());
+    else build_clover(c);
+}
+}  // namespace mgeig
 
 extern "C" {
 
@@ -110,6 +122,10 @@ void mgeig_default_params(mgeig_params *p) {
     p->ritz_keep = 1e-6;
     p->fine_deflate = 1;
     p->fine_deflate_radius = -1.0;
+    p->adaptive_tol = 1;
+    p->ritz_start = 1;
+    p->coarse_links = MGEIG_LINKS_LEVEL;
+    p->barrier_timeout = 2.0;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
@@ -144,6 +160,7 @@ int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
         c.clov32.alloc((size_t)V * 18 * 16);
         c.staging.alloc((size_t)V * 4 * 9 * 16);   // largest host-layout transfer: the gauge field
         ensure_reduction(c, 64);
+        noalloc_prepare(c);
         return MGEIG_OK;
     });
     if (rc != MGEIG_OK) {
@@ -161,8 +178,9 @@ void mgeig_destroy(mgeig_ctx *ctx) {
     if (c.stream) cudaStreamSynchronize(c.stream);
     try { c.timer.reset(); } catch (...) {}
     mg_free(c);
-    c.U64.free(); c.U32.free(); c.clov64.free(); c.clov32.free(); c.staging.free();
-    c.red_partial.free(); c.red_out.free(); c.Dc.free();
+    net_free(c);
+    c.U64.free(); c.U32.free(); c.clov64.free(); c.clov32.free(); c.clov_user.free(); c.staging.free();
+    c.red_partial.free(); c.red_out.free(); c.Dc.free(); c.Dc16.free(); c.Dcs.free();
     for (auto &b : c.user_bufs) b.free();
     if (c.pinned) cudaFreeHost(c.pinned);
     if (c.stream) cudaStreamDestroy(c.stream);
@@ -186,7 +204,7 @@ int mgeig_set_params(mgeig_ctx *ctx, const mgeig_params *p) {
         c.sap_vol = p->sap_block[0] * p->sap_block[1] * p->sap_block[2] * p->sap_block[3];
         c.sap_nblk = (int)(c.g.V / c.sap_vol);
         c.have_setup = false;
-        if (c.have_gauge) build_clover(c);
+        if (c.have_gauge) refresh_clover(c);
         mg_alloc(c);
         sync(c);
         return MGEIG_OK;
@@ -198,6 +216,8 @@ int mgeig_load_gauge(mgeig_ctx *ctx, const double *U) {
     return guarded(ctx, [&](Ctx &c) {
         MG_CUDA(cudaMemcpyAsync(c.staging.p, U, (size_t)c.g.V * 4 * 9 * 16, cudaMemcpyHostToDevice, c.stream));
         pack_gauge(c, c.staging.as<double>());
+        c.clover_loaded = false;
+        c.clov_user.free();
         build_clover(c);
         c.have_gauge = true;
         c.have_setup = false;
@@ -210,8 +230,31 @@ int mgeig_load_gauge_dev(mgeig_ctx *ctx, const void *U_dev) {
     if (!ctx || !U_dev) return MGEIG_EINVAL;
     return guarded(ctx, [&](Ctx &c) {
         pack_gauge(c, static_cast<const double *>(U_dev));
+        c.clover_loaded = false;
+        c.clov_user.free();
         build_clover(c);
         c.have_gauge = true;
+        c.have_setup = false;
+        sync(c);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_load_clover(mgeig_ctx *ctx, const double *A) {
+    if (!ctx) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_gauge) return MGEIG_ENOTSETUP;
+        sync(c);
+        if (A) {
+            const size_t bytes = (size_t)c.g.V * 72 * 16;
+            c.clov_user.alloc(bytes);
+            MG_CUDA(cudaMemcpyAsync(c.clov_user.p, A, bytes, cudaMemcpyHostToDevice, c.stream));
+            c.clover_loaded = true;
+        } else {
+            c.clover_loaded = false;
+            c.clov_user.free();
+        }
+        refresh_clover(c);
         c.have_setup = false;
         sync(c);
         return MGEIG_OK;
@@ -296,21 +339,21 @@ int mgeig_apply(mgeig_ctx *ctx, double sigma, int op, int prec, const double *x,
     return guarded(ctx, [&](Ctx &c) {
         if (!c.have_gauge) return MGEIG_ENOTSETUP;
         const int mode = op == MGEIG_OP_Q ? MODE_QSIGMA : MODE_DSIGMA;
+        const size_t sb = spinor_bytes(c);
         TmpBuf a, b, a32, b32;
-        a.alloc(spinor_bytes(c));
-        b.alloc(spinor_bytes(c));
-        if (prec == MGEIG_PREC_F32) { a32.alloc(spinor_bytes(c) / 2); b32.alloc(spinor_bytes(c) / 2); }
+        a.alloc(sb * nrhs);
+        b.alloc(sb * nrhs);
+        if (prec == MGEIG_PREC_F32) { a32.alloc(sb / 2 * nrhs); b32.alloc(sb / 2 * nrhs); }
         for (int r = 0; r < nrhs; ++r) {
-            const size_t off = (size_t)r * c.fine_ncpx() * 2;
-            host_to_internal(c, x + off, a.p);
-            if (prec == MGEIG_PREC_F64) {
-                apply_fine<double>(c, mode, sigma, a.p, b.p);
-            } else {
-                convert_f64_to_f32(c, a.p, a32.p, c.fine_ncpx());
-                apply_fine<float>(c, mode, sigma, a32.p, b32.p);
-                convert_f32_to_f64(c, b32.p, b.p, c.fine_ncpx());
-            }
-            internal_to_host(c, b.p, y + off);
+            host_to_internal(c, x + (size_t)r * c.fine_ncpx() * 2, a.as<char>() + sb * r);
+            if (prec == MGEIG_PREC_F32) convert_f64_to_f32(c, a.as<char>() + sb * r, a32.as<char>() + sb / 2 * r, c.fine_ncpx());
+        }
+        // all right-hand sides in one launch (links and clover read once for all)
+        if (prec == MGEIG_PREC_F64) apply_fine_nrhs<double>(c, mode, sigma, a.p, b.p, nrhs);
+        else apply_fine_nrhs<float>(c, mode, sigma, a32.p, b32.p, nrhs);
+        for (int r = 0; r < nrhs; ++r) {
+            if (prec == MGEIG_PREC_F32) convert_f32_to_f64(c, b32.as<char>() + sb / 2 * r, b.as<char>() + sb * r, c.fine_ncpx());
+            internal_to_host(c, b.as<char>() + sb * r, y + (size_t)r * c.fine_ncpx() * 2);
         }
         a.free(); b.free(); a32.free(); b32.free();
         return MGEIG_OK;
@@ -325,6 +368,21 @@ int mgeig_apply_dev(mgeig_ctx *ctx, double sigma, int op, int prec, const void *
         const int mode = op == MGEIG_OP_Q ? MODE_QSIGMA : MODE_DSIGMA;
         if (prec == MGEIG_PREC_F64) apply_fine<double>(c, mode, sigma, x, y);
         else apply_fine<float>(c, mode, sigma, x, y);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_apply_dev_nrhs(mgeig_ctx *ctx, double sigma, int op, int prec, const void *x, void *y, int nrhs) {
+    if (!ctx || !x || !y || nrhs < 1) return MGEIG_EINVAL;
+    if (check_op(op, prec) != MGEIG_OK) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_gauge) return MGEIG_ENOTSETUP;
+        const size_t fb = c.fine_ncpx() * (prec == MGEIG_PREC_F64 ? 16 : 8) * (size_t)nrhs;
+        const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
+        if (xb < yb + fb && yb < xb + fb) return MGEIG_EINVAL;   // the fields must not overlap
+        const int mode = op == MGEIG_OP_Q ? MODE_QSIGMA : MODE_DSIGMA;
+        if (prec == MGEIG_PREC_F64) apply_fine_nrhs<double>(c, mode, sigma, x, y, nrhs);
+        else apply_fine_nrhs<float>(c, mode, sigma, x, y, nrhs);
         return MGEIG_OK;
     });
 }
@@ -455,6 +513,44 @@ int mgeig_coarse_apply(mgeig_ctx *ctx, double sigma, const double *xc, double *y
     });
 }
 
+int mgeig_coarse_apply_nrhs(mgeig_ctx *ctx, double sigma, const double *xc, double *yc, int nrhs) {
+    if (!xc || !yc || nrhs < 1 || nrhs > 16) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        const size_t n = c.coarse_ncpx(), b64 = n * 16 * nrhs;
+        TmpBuf a, b, a32, b32;
+        a.alloc(b64);
+        b.alloc(b64);
+        MG_CUDA(cudaMemcpyAsync(a.p, xc, b64, cudaMemcpyHostToDevice, c.stream));
+        if (c.mixed()) {
+            a32.alloc(b64 / 2);
+            b32.alloc(b64 / 2);
+            coarse_flat_convert(c, a.p, a32.p, n * nrhs, true);
+            coarse_apply_nrhs(c, sigma, a32.p, b32.p, nrhs);
+            coarse_flat_convert(c, b32.p, b.p, n * nrhs, false);
+        } else {
+            for (int r = 0; r < nrhs; ++r)
+                coarse_apply<double>(c, c.Dc.p, sigma, a.as<char>() + n * 16 * r, b.as<char>() + n * 16 * r, false);
+        }
+        MG_CUDA(cudaMemcpyAsync(yc, b.p, b64, cudaMemcpyDeviceToHost, c.stream));
+        sync(c);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_coarse_apply_dev_nrhs(mgeig_ctx *ctx, double sigma, const void *X, void *Y, int nrhs) {
+    if (!X || !Y || nrhs < 1 || nrhs > 16) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        if (!c.mixed()) return MGEIG_EINVAL;
+        const size_t fb = c.coarse_ncpx() * 8 * (size_t)nrhs;
+        const char *xb = static_cast<const char *>(X), *yb = static_cast<const char *>(Y);
+        if (xb < yb + fb && yb < xb + fb) return MGEIG_EINVAL;
+        coarse_apply_nrhs(c, sigma, X, Y, nrhs);
+        return MGEIG_OK;
+    });
+}
+
 int mgeig_sap(mgeig_ctx *ctx, double sigma, const double *b, double *z, int cycles) {
     if (!b || !z || cycles < 0) return MGEIG_EINVAL;
     return guarded(ctx, [&](Ctx &c) {
@@ -480,6 +576,7 @@ int mgeig_mg_cycle(mgeig_ctx *ctx, double sigma, const double *r, double *z) {
         host_to_internal(c, r, a.p);
         mg_cycle_host(c, sigma, a.as<double>(), b.as<double>());
         internal_to_host(c, b.p, z);
+        coarse_iters_take(c);   // raises the coarse solver's timeout or breakdown
         return MGEIG_OK;
     });
 }
@@ -489,6 +586,10 @@ int mgeig_mg_cycle_dev_noalloc(mgeig_ctx *ctx, double sigma, const void *r, void
     return guarded(ctx, [&](Ctx &c) {
         if (!c.have_setup) return MGEIG_ENOTSETUP;
         if (c.prm.smoother != MGEIG_SAP || c.timer.on) return MGEIG_EINVAL;
+        // the prolongation writes z before the smoother reads r: they must not overlap
+        const size_t nb = c.fine_ncpx() * 2 * c.level_bytes();
+        const char *rb = static_cast<const char *>(r), *zb = static_cast<const char *>(z);
+        if (rb < zb + nb && zb < rb + nb) return MGEIG_EINVAL;
         return mg_cycle_noalloc(c, sigma, r, z);
     });
 }
@@ -546,7 +647,7 @@ int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms, d
     static const char *kNames[K_NCLASS] = {"stencil_f64", "stencil_f32", "sap_f64",      "sap_f32",
                                            "restrict",    "prolong",     "coarse_apply", "coarse_build",
                                            "interp_build", "blas_f64",   "blas_low",     "other",
-                                           "coarse_gmres"};
+                                           "coarse_gmres", "net"};
     return guarded(ctx, [&](Ctx &c) {
         c.timer.flush();
         for (int k = 0; k < n && k < K_NCLASS; ++k) {
@@ -556,6 +657,73 @@ int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms, d
             if (names) names[k] = kNames[k];
         }
         return (int)K_NCLASS;
+    });
+}
+
+int mgeig_net_init(mgeig_ctx *ctx, uint64_t seed) {
+    return guarded(ctx, [&](Ctx &c) {
+        net_init(c, seed);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_net_set_weights(mgeig_ctx *ctx, const float *W) {
+    if (!W) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        net_set_weights(c, W);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_net_get_weights(mgeig_ctx *ctx, float *W) {
+    if (!W) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        net_get_weights(c, W);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_net_train(mgeig_ctx *ctx, int steps, int batch, double lr, uint64_t seed, double *losses) {
+    if (steps < 1 || batch < 1 || batch > 64 || !(lr > 0)) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        if (!c.mixed() || !net_supported(c)) return MGEIG_EINVAL;
+        net_train(c, steps, batch, lr, seed, losses);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_net_loss_grads(mgeig_ctx *ctx, const double *x, const double *t, int batch, double *loss, float *G) {
+    if (!x || !t || !loss || !G || batch < 1 || batch > 64) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        *loss = net_loss_grads(c, x, t, batch, G);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_net_apply(mgeig_ctx *ctx, const double *r, double *e) {
+    if (!r || !e) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        const size_t sb = spinor_bytes(c);
+        TmpBuf a, a32, z32;
+        a.alloc(sb);
+        a32.alloc(sb / 2);
+        z32.alloc(sb / 2);
+        host_to_internal(c, r, a.p);
+        convert_f64_to_f32(c, a.p, a32.p, c.fine_ncpx());
+        MG_CUDA(cudaMemsetAsync(z32.p, 0, sb / 2, c.stream));
+        net_smooth(c, a32.p, z32.p);
+        convert_f32_to_f64(c, z32.p, a.p, c.fine_ncpx());
+        internal_to_host(c, a.p, e);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_fma_peak(mgeig_ctx *ctx, int prec, int reps, double *flops) {
+    if (!ctx || !flops || reps < 1 || (prec != MGEIG_PREC_F64 && prec != MGEIG_PREC_F32)) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        *flops = fma_peak_flops(c, prec, reps);
+        return MGEIG_OK;
     });
 }
 

@@ -13,22 +13,40 @@
 //    (gamma5^c A = D_c - sigma gamma5^c, Eq. 2.6 with a shift), whose spectrum
 //    lies in the right half plane instead of around the origin.
 //
-// Grid: G co-resident blocks; block b owns a contiguous slice of coarse rows.
-// One Arnoldi step = the coarse matvec on the owned rows (reading neighbour rows
-// written before the last grid barrier), the deflation projection, two classical
-// Gram-Schmidt passes and a norm in TWO grid-wide reductions: the deflation
-// coefficients W^dag u and the first pass are reduced together, since
-// <v_i, g5 (u - A W t)> = <g5 v_i, u> - sum_l t_l F_il with F_il = <g5 v_i, A W_l>
-// (row i reduced when v_i is made); the second pass and the norm go together,
-// ||w2||^2 = ||w1||^2 - ||h2||^2.  Partial sums go to
-// a [G][slots] buffer; after each barrier every block adds the G partials in the
-// same order, so all blocks hold bit-identical scalars and run the Givens
-// rotations and the triangular solve redundantly (deterministic, no extra
-// barrier).  Basis vectors stay unnormalised with one scale factor each.
+// Grid: G co-resident blocks; block b owns a contiguous slice of rb coarse rows.
+// Every vector the block only ever reads or writes on its own rows (the Krylov
+// basis V_i, the raw products U_i = A s_i V_i, the right-hand side, the iterate,
+// a work vector, and when room is left the deflation vectors W, A W) lives in
+// the block's shared memory (in a per-block slice of global scratch when the
+// coarse grid is too large for that); only the vector being multiplied goes to
+// global memory (`pub`), where the matvecs of the neighbouring blocks read it.
+//
+// One Arnoldi step, classical Gram-Schmidt with a second pass, two grid-wide
+// reductions:
+//   u     = A s_j V_j                          (matvec of pub, see below)
+//   R1:   a_l = <W_l, u>, b_i = <g5 s_i V_i, u>, f_l = <g5 s_j V_j, A W_l>
+//   t     = E^-1 a;  h1_i = b_i - sum_l F_il t_l   (F_il = <g5 s_i V_i, A W_l>)
+//   w1    = g5 (u - A W t) - sum_i h1_i s_i V_i;  pub <- w1
+//   R2:   h2_i = <s_i V_i, w1>, ||w1||^2  (||w2||^2 = ||w1||^2 - ||h2||^2)
+//   V_j+1 = w1 - sum_i h2_i s_i V_i  (own rows only)
+// The next matvec reads w1 from pub, complete on every block after the R2
+// barrier, and corrects it on its own rows with the stored products:
+// A s_j+1 V_j+1 = s_j+1 (A w1 - sum_i h2_i U_i).  So no block ever reads a
+// vector that another block is still writing, with two grid barriers per step.
+// Partial sums go to a [G][slots] buffer (consecutive reductions use disjoint
+// slots); after each barrier every block adds the G partials in the same
+// order, so all blocks hold bit-identical scalars and run the Givens rotations
+// and the triangular solve redundantly.  Basis vectors stay unnormalised with
+// one scale factor each.
 //
 // The grid barrier spins on a generation counter with a clock64() budget; on
 // expiry it raises a sticky error word (the kernel then returns without further
 // waits) that the host reads at its next synchronisation (MGEIG_ETIMEOUT).
+#include <array>
+#include <map>
+#include <mutex>
+
+#include "half16.cuh"
 #include "internal.h"
 
 namespace mgeig {
@@ -40,6 +58,8 @@ constexpr int CG_MAXK = 24;                       // deflation vectors (= max N_
 constexpr int WS = 2 * CG_MAXK + CG_MAXM + 2;     // values of one reduction
 constexpr int OFF_S1 = 0, OFF_S2 = WS, OFF_N = 2 * WS, OFF_P = 2 * WS + 2;
 constexpr int CG_SLOTS = OFF_P + CG_MAXK;
+// shared memory a block may use in all (static + dynamic), with a reserve
+constexpr size_t CG_SMEM_LIMIT = 227 * 1024 - 1024;
 
 struct CGState {
     unsigned int count;   // barrier arrivals (returns to 0 after every barrier)
@@ -56,14 +76,18 @@ template <> struct Pod2<double> { using T = double2; };
 template <typename R>
 struct CGArgs {
     int nagg, ntv, n;              // coarse sites, test vectors, rows = nagg * 2 ntv
-    int cd[4];                     // coarse lattice extents
+    int rb;                        // rows per block (the last block may own fewer)
+    int nslice;                    // owned-row vectors per block: V (m+1), U (m+1), rhs, x, w
+    int smem_slices, smem_defl;    // 1: the slices / copies of W, A W live in shared memory
     const cpx<R> *Dc;              // [9][nagg][col][row]
+    const void *L16;               // 16-bit links [9][nagg][re|im][row][col] (16-bit kernels)
+    const float *Ls;               // their scales [9][nagg]
     const int *nbr;                // [9][nagg] neighbour aggregates
     R sigma;
     const cpx<R> *b;               // r_c
-    cpx<R> *x;                     // e (output); holds y during the iteration
-    cpx<R> *rhs;                   // gamma5^c Pi r_c (scratch, n)
-    cpx<R> *V;                     // (m + 1) x n
+    cpx<R> *x;                     // e (output)
+    cpx<R> *pub;                   // the vector being multiplied (n)
+    cpx<R> *gslices;               // G x nslice x rb, when the slices are not in shared memory
     int k;                         // deflation vectors (0: none)
     const cpx<R> *W, *AW;          // k x n each
     const double2 *Einv;           // k x k, row-major
@@ -111,14 +135,14 @@ __device__ __forceinline__ cpx<double> ldcg(const cpx<double> *p) {
     return cpx<double>(v.x, v.y);
 }
 
-// u[t] = ((Q_c - sigma)(s v))[t] = ((gamma5^c D_c - sigma)(s v))[t] for the rows
-// t in [r0, r1); a group of TPR consecutive threads shares one row: lane q takes
-// the columns j = q (mod TPR) of all nine hop blocks, and the group reduces with
-// shuffles.
+// out[t - r0] = ((Q_c - sigma)(s v))[t] = ((gamma5^c D_c - sigma)(s v))[t] for the
+// owned rows t in [r0, r1), v = the published vector; a group of TPR consecutive
+// threads shares one row: lane q takes the columns j = q (mod TPR) of all nine
+// hop blocks, and the group reduces with shuffles.
 constexpr int TPR = 8;
 
 template <typename R>
-__device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *u, int r0, int r1) {
+__device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1) {
     const int n2 = 2 * a.ntv;
     const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
     for (int tb = r0; tb < r1; tb += ngrp) {
@@ -166,28 +190,91 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
         }
         if (t < r1 && q == 0) {
             if ((t % n2) >= a.ntv) acc = -acc;
-            u[t] = s * acc - (a.sigma * s) * ldcg(v + t);
+            out[t - r0] = s * acc - (a.sigma * s) * ldcg(v + t);
         }
     }
 }
 
-template <typename R>
-__device__ __forceinline__ cpx<R> g5c(const CGArgs<R> &a, int t, cpx<R> v) {
-    return (t % (2 * a.ntv)) >= a.ntv ? -v : v;
+// The same product with 16-bit links (FP32 vectors and arithmetic): lane q takes
+// the column pairs p = q (mod TPR) of the real and imaginary planes, and every
+// hop block's sum is multiplied by the block's scale.
+template <typename H>
+__device__ __forceinline__ void qmatvec16(const CGArgs<float> &a, const cpx<float> *v, float s, cpx<float> *out,
+                                          int r0, int r1) {
+    using HP = typename H16<H>::P;
+    const int n2 = 2 * a.ntv, np = a.ntv;
+    const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
+    constexpr int U = (CG_MAXK + TPR - 1) / TPR;   // pairs per lane (n2 / 2 <= CG_MAXK)
+    const H *L = static_cast<const H *>(a.L16);
+    for (int tb = r0; tb < r1; tb += ngrp) {
+        const int t = tb + grp;
+        float ar = 0.f, ai = 0.f;
+        if (t < r1) {
+            const int site = t / n2, row = t % n2;
+            for (int d = 0; d < 9; ++d) {
+                const size_t blk = (size_t)d * a.nagg + site;
+                const int nb = __ldg(a.nbr + blk);
+                const HP *pr = reinterpret_cast<const HP *>(L + blk * 2 * n2 * n2 + (size_t)row * n2);
+                const HP *pi = pr + (size_t)n2 * n2 / 2;
+                const float4 *xb = reinterpret_cast<const float4 *>(v + (size_t)nb * n2);
+                HP rv[U], iv[U];
+                float4 xv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int p = q + u * TPR;
+                    if (p < np) { rv[u] = pr[p]; iv[u] = pi[p]; xv[u] = __ldcg(xb + p); }
+                }
+                float dr = 0.f, di = 0.f;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (q + u * TPR < np) {
+                        const float2 r = H16<H>::pair(rv[u]), im = H16<H>::pair(iv[u]);
+                        const float4 x = xv[u];
+                        dr = fmaf(r.x, x.x, dr); dr = fmaf(-im.x, x.y, dr);
+                        di = fmaf(r.x, x.y, di); di = fmaf(im.x, x.x, di);
+                        dr = fmaf(r.y, x.z, dr); dr = fmaf(-im.y, x.w, dr);
+                        di = fmaf(r.y, x.w, di); di = fmaf(im.y, x.z, di);
+                    }
+                }
+                const float sc = __ldg(a.Ls + blk);
+                ar = fmaf(sc, dr, ar);
+                ai = fmaf(sc, di, ai);
+            }
+        }
+        for (int o = 1; o < TPR; o <<= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (t < r1 && q == 0) {
+            cpx<float> acc(ar, ai);
+            if ((t % n2) >= a.ntv) acc = -acc;
+            out[t - r0] = s * acc - (a.sigma * s) * ldcg(v + t);
+        }
+    }
+}
+
+// the product of the kernel's link format LK (0: level precision, 1: BF16, 2: FP16)
+template <typename R, int LK>
+__device__ __forceinline__ void matvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1) {
+    if constexpr (LK == 0) qmatvec<R>(a, v, s, out, r0, r1);
+    else if constexpr (LK == 1) qmatvec16<__nv_bfloat16>(a, v, s, out, r0, r1);
+    else qmatvec16<__half>(a, v, s, out, r0, r1);
 }
 
 // Scalars (partial sums, Hessenberg matrix, Givens rotations, E^-1) are kept in
 // the solver's own precision R: FP32 in the mixed-precision preconditioner,
 // where FP64 arithmetic (1/64 of the FP32 rate on this part) held most warps at
 // block barriers, FP64 in the all-FP64 path.
-template <typename R>
+template <typename R, int LK>
 __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a) {
     using P = typename Pod2<R>::T;
     auto P2 = [](R x, R y) { return P{x, y}; };
+    extern __shared__ __align__(16) unsigned char cg_dyn[];
     __shared__ P wpart[WS];                    // this block's partial sums
     __shared__ P h[WS];                        // grid-wide sums after a gather
     __shared__ P F[CG_MAXM * CG_MAXK];         // F_il = <g5 s_i V_i, A W_l>
     __shared__ P h1[CG_MAXM];
+    __shared__ P h2s[CG_MAXM];                 // second-pass coefficients of the last step
     __shared__ R nsum[CG_THREADS / 32];
     __shared__ R nrm2s;
     __shared__ P Rm[(CG_MAXM + 1) * CG_MAXM];  // rotated Hessenberg, column-major
@@ -200,24 +287,45 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     const unsigned int G = gridDim.x;
     const int nw = CG_THREADS / 32;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int rows_per_block = (a.n + G - 1) / G;
-    const int r0 = blockIdx.x * rows_per_block;
-    const int r1 = min(a.n, r0 + rows_per_block);
+    const int rb = a.rb;
+    const int r0 = min(a.n, (int)blockIdx.x * rb);
+    const int r1 = min(a.n, r0 + rb);
+    const int nr = r1 - r0;
+    const int m = a.m, k = a.k, n2 = 2 * a.ntv;
     P *mypart = a.partial + (size_t)blockIdx.x * CG_SLOTS;
-    const int k = a.k;
+
+    // owned-row slices: V_0..V_m, U_0..U_m, rhs, x, w
+    cpx<R> *S = a.smem_slices ? reinterpret_cast<cpx<R> *>(cg_dyn)
+                              : a.gslices + (size_t)blockIdx.x * a.nslice * rb;
+    auto Vv = [&](int i) { return S + (size_t)i * rb; };
+    auto Uv = [&](int i) { return S + (size_t)(m + 1 + i) * rb; };
+    cpx<R> *rhs = S + (size_t)(2 * m + 2) * rb;
+    cpx<R> *xs = rhs + rb;
+    cpx<R> *ws = xs + rb;
+    cpx<R> *Dl = a.smem_defl ? reinterpret_cast<cpx<R> *>(cg_dyn) + (size_t)a.nslice * rb : nullptr;
+    auto Wv = [&](int l) -> const cpx<R> * { return Dl ? Dl + (size_t)l * rb : a.W + (size_t)l * a.n + r0; };
+    auto AWv = [&](int l) -> const cpx<R> * { return Dl ? Dl + (size_t)(k + l) * rb : a.AW + (size_t)l * a.n + r0; };
+    auto g5 = [&](int i, cpx<R> v) { return ((r0 + i) % n2) >= a.ntv ? -v : v; };
 
     for (int i = threadIdx.x; i < k * k; i += blockDim.x) Ei[i] = P2((R)a.Einv[i].x, (R)a.Einv[i].y);
     if (threadIdx.x < CG_MAXK) { tc[threadIdx.x] = P2(0, 0); t0[threadIdx.x] = P2(0, 0); }
+    if (Dl)
+        for (int e = threadIdx.x; e < k * nr; e += blockDim.x) {
+            const int l = e / nr, i = e % nr;
+            Dl[(size_t)l * rb + i] = a.W[(size_t)l * a.n + r0 + i];
+            Dl[(size_t)(k + l) * rb + i] = a.AW[(size_t)l * a.n + r0 + i];
+        }
     __syncthreads();
 
     // wpart[i] = sc_i <X_i, u> over the owned rows, i < cnt: warp i takes value i,
-    // its lanes stride over the rows (u complete on the owned rows)
-    auto dots = [&](int cnt, auto vec, auto sc, const cpx<R> *u) {
+    // its lanes stride over the rows
+    auto dots = [&](int cnt, int base, auto vec, auto sc, const cpx<R> *u, bool g5x) {
         for (int i = wp; i < cnt; i += nw) {
             const cpx<R> *xi = vec(i);
             R sr = 0, si = 0;
-            for (int t = r0 + lane; t < r1; t += 32) {
+            for (int t = lane; t < nr; t += 32) {
                 cpx<R> p = xi[t], q = u[t];
+                if (g5x) p = g5(t, p);
                 sr += p.re * q.re + p.im * q.im;
                 si += p.re * q.im - p.im * q.re;
             }
@@ -225,7 +333,23 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 si += __shfl_xor_sync(0xffffffffu, si, o);
             }
-            if (lane == 0) wpart[i] = P2(sr * sc(i), si * sc(i));
+            if (lane == 0) wpart[base + i] = P2(sr * sc(i), si * sc(i));
+        }
+    };
+    // wpart[slot] = ||v||^2 over the owned rows
+    auto norm_part = [&](const cpx<R> *v, int slot) {
+        R acc = 0;
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+            cpx<R> q = v[t];
+            acc += q.re * q.re + q.im * q.im;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) nsum[wp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            R s2 = 0;
+            for (int w = 0; w < nw; ++w) s2 += nsum[w];
+            wpart[slot] = P2(s2, 0);
         }
     };
     // publish wpart[0..cnt) to this block's partial slots, barrier, h = grid sums
@@ -248,37 +372,38 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         __syncthreads();
         return true;
     };
-    // u[t] = f(t, u[t], sum_i coef_i X_i[t]) on the owned rows; TPR lanes share a row
+    // u[i] = f(i, u[i], sum_l coef_l X_l[i]) on the owned rows; TPR lanes share a row
     auto combine = [&](int cnt, auto vec, auto coef, cpx<R> *u, auto f) {
         const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
-        for (int tb = r0; tb < r1; tb += ngrp) {
-            const int t = tb + grp;
+        for (int ib = 0; ib < nr; ib += ngrp) {
+            const int i = ib + grp;
             cpx<R> acc0, acc1;
-            if (t < r1) {
-                int i = q;
-                for (; i + TPR < cnt; i += 2 * TPR) {
-                    cmac(acc0, coef(i), vec(i)[t]);
-                    cmac(acc1, coef(i + TPR), vec(i + TPR)[t]);
+            if (i < nr) {
+                int l = q;
+                for (; l + TPR < cnt; l += 2 * TPR) {
+                    cmac(acc0, coef(l), vec(l)[i]);
+                    cmac(acc1, coef(l + TPR), vec(l + TPR)[i]);
                 }
-                if (i < cnt) cmac(acc0, coef(i), vec(i)[t]);
+                if (l < cnt) cmac(acc0, coef(l), vec(l)[i]);
             }
             cpx<R> acc = acc0 + acc1;
             for (int o = 1; o < TPR; o <<= 1) {
                 acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
                 acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
             }
-            if (t < r1 && q == 0) u[t] = f(t, u[t], acc);
+            if (i < nr && q == 0) u[i] = f(i, u[i], acc);
         }
         __syncthreads();
     };
+    auto publish = [&](const cpx<R> *v) {
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) a.pub[r0 + i] = v[i];
+    };
     auto one = [](int) { return R(1); };
-    auto Wvec = [&](int i) { return a.W + (size_t)i * a.n; };
-    auto AWvec = [&](int i) { return a.AW + (size_t)i * a.n; };
-    auto Vvec = [&](int i) { return a.V + (size_t)i * a.n; };
+    auto tcoef = [&](int l) { return cpx<R>((R)tc[l].x, (R)tc[l].y); };
 
     // tc = E^-1 W^dag u
     auto deflation_coeffs = [&](const cpx<R> *u) -> bool {
-        dots(k, Wvec, one, u);
+        dots(k, 0, Wv, one, u, false);
         if (!reduce(OFF_P, k)) return false;
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
             R sr = 0, si = 0;
@@ -294,64 +419,50 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     };
     // u <- gamma5^c (u - A W tc)
     auto project_g5 = [&](cpx<R> *u) {
-        combine(k, AWvec, [&](int i) { return cpx<R>((R)tc[i].x, (R)tc[i].y); }, u,
-                [&](int t, cpx<R> ut, cpx<R> s) { return g5c(a, t, ut - s); });
-    };
-    // u = gamma5^c Pi (Q_c - sigma)(s v) on the owned rows
-    auto apply_op = [&](const cpx<R> *v, R s, cpx<R> *u) -> bool {
-        qmatvec<R>(a, v, s, u, r0, r1);
-        __syncthreads();
-        if (k > 0 && !deflation_coeffs(u)) return false;
-        project_g5(u);
-        return true;
-    };
-    // h[0] = ||v||^2 over the grid
-    auto grid_norm2 = [&](const cpx<R> *v) -> bool {
-        R acc = 0;
-        for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-            cpx<R> q = v[t];
-            acc += q.re * q.re + q.im * q.im;
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) nsum[wp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            R s2 = 0;
-            for (int w = 0; w < nw; ++w) s2 += nsum[w];
-            wpart[0] = P2(s2, 0);
-        }
-        return reduce(OFF_N, 1);
+        combine(k, AWv, tcoef, u, [&](int i, cpx<R> ui, cpx<R> s) { return g5(i, ui - s); });
     };
 
     // rhs = gamma5^c Pi r_c, t0 = E^-1 W^dag r_c, x = 0.  The tolerance refers
     // to ||r_c||: when r_c lies mostly in span(W) the projected right-hand side
     // is small and needs no further reduction.
-    for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) { a.rhs[t] = a.b[t]; a.x[t] = cpx<R>(); }
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) { rhs[i] = a.b[r0 + i]; xs[i] = cpx<R>(); }
     __syncthreads();
-    if (!grid_norm2(a.rhs)) return;
+    norm_part(rhs, 0);
+    if (!reduce(OFF_N, 1)) return;
     if (threadIdx.x == 0) bnorm = sqrt(h[0].x);
     __syncthreads();
     if (k > 0) {
-        if (!deflation_coeffs(a.rhs)) return;
+        if (!deflation_coeffs(rhs)) return;
         for (int i = threadIdx.x; i < k; i += blockDim.x) t0[i] = tc[i];
         __syncthreads();
     }
-    project_g5(a.rhs);
+    project_g5(rhs);
     if (threadIdx.x == 0) stop = !(bnorm > 0) || !isfinite(bnorm);
     __syncthreads();
     const R tol_abs = (R)a.tol * bnorm;
     int its = 0;
     bool have_x = false;
     while (!stop && its < a.maxiter) {
+        cpx<R> *v0 = Vv(0);
         // V0 = rhs - op(x)  (or rhs)
         if (have_x) {
-            if (!apply_op(a.x, R(1), a.V)) return;
-            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) a.V[t] = a.rhs[t] - a.V[t];
+            publish(xs);
+            if (!grid_sync(a.st, G, a.timeout)) return;       // x complete everywhere
+            matvec<R, LK>(a, a.pub, R(1), v0, r0, r1);
+            __syncthreads();
+            if (k > 0) {
+                if (!deflation_coeffs(v0)) return;             // its barrier also ends the reads of pub
+            } else if (!grid_sync(a.st, G, a.timeout)) {
+                return;                                        // every matvec done before pub changes
+            }
+            combine(k, AWv, tcoef, v0, [&](int i, cpx<R> vi, cpx<R> s) { return rhs[i] - g5(i, vi - s); });
         } else {
-            for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) a.V[t] = a.rhs[t];
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) v0[i] = rhs[i];
+            __syncthreads();
         }
-        __syncthreads();
-        if (!grid_norm2(a.V)) return;
+        publish(v0);
+        norm_part(v0, 0);
+        if (!reduce(OFF_N, 1)) return;                         // also makes V0 visible in pub
         if (threadIdx.x == 0) {
             beta = sqrt(h[0].x);
             stop = !(beta > tol_abs) || !isfinite(beta);
@@ -362,36 +473,27 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         }
         __syncthreads();
         if (stop) break;
-        const int mm = min(a.m, a.maxiter - its);
+        const int mm = min(m, a.maxiter - its);
         int kk = 0;
         bool conv = false;
         for (int j = 0; j < mm; ++j) {
-            cpx<R> *w = a.V + (size_t)(j + 1) * a.n;
-            const cpx<R> *vj = Vvec(j);
-            // u = (Q_c - sigma) s_j V_j on the owned rows
-            qmatvec<R>(a, vj, (R)scale[j], w, r0, r1);
+            cpx<R> *uj = Uv(j);
+            const cpx<R> *vj = Vv(j);
+            // U_j = A s_j V_j: the matvec of pub (= V_j before its second pass),
+            // corrected by the second-pass coefficients of the last step
+            matvec<R, LK>(a, a.pub, (R)scale[j], uj, r0, r1);
             __syncthreads();
+            if (j > 0)
+                combine(j, Uv, [&](int i) { return cpx<R>((R)(h2s[i].x * scale[j]), (R)(h2s[i].y * scale[j])); },
+                        uj, [](int, cpx<R> ui, cpx<R> s) { return ui - s; });
             // reduction 1: a_l = <W_l, u>, b_i = <g5 s_i V_i, u>, f_l = <g5 s_j V_j, A W_l>
-            dots(k, Wvec, one, w);
-            for (int i = wp; i <= j; i += nw) {
-                const cpx<R> *vi = Vvec(i);
-                R sr = 0, si = 0;
-                for (int t = r0 + lane; t < r1; t += 32) {
-                    cpx<R> pv = g5c(a, t, vi[t]), q = w[t];
-                    sr += pv.re * q.re + pv.im * q.im;
-                    si += pv.re * q.im - pv.im * q.re;
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                    si += __shfl_xor_sync(0xffffffffu, si, o);
-                }
-                if (lane == 0) wpart[k + i] = P2(sr * scale[i], si * scale[i]);
-            }
+            dots(k, 0, Wv, one, uj, false);
+            dots(j + 1, k, Vv, [&](int i) { return scale[i]; }, uj, true);
             for (int l = wp; l < k; l += nw) {
-                const cpx<R> *awl = AWvec(l);
+                const cpx<R> *awl = AWv(l);
                 R sr = 0, si = 0;
-                for (int t = r0 + lane; t < r1; t += 32) {
-                    cpx<R> pv = g5c(a, t, vj[t]), q = awl[t];
+                for (int t = lane; t < nr; t += 32) {
+                    cpx<R> pv = g5(t, vj[t]), q = awl[t];
                     sr += pv.re * q.re + pv.im * q.im;
                     si += pv.re * q.im - pv.im * q.re;
                 }
@@ -425,40 +527,30 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
                 Rm[j * (CG_MAXM + 1) + i] = b;
             }
             __syncthreads();
-            // w1 = g5 (u - A W t) - sum_i h1_i s_i V_i
-            combine(k, AWvec, [&](int i) { return cpx<R>((R)tc[i].x, (R)tc[i].y); }, w,
-                    [&](int t, cpx<R> ut, cpx<R> sm) { return g5c(a, t, ut - sm); });
-            combine(j + 1, Vvec, [&](int i) { return cpx<R>((R)(h1[i].x * scale[i]), (R)(h1[i].y * scale[i])); }, w,
-                    [](int, cpx<R> ut, cpx<R> sm) { return ut - sm; });
+            // w1 = g5 (u - A W t) - sum_i h1_i s_i V_i, published for the next matvec
+            combine(k, AWv, tcoef, ws, [&](int i, cpx<R>, cpx<R> s) { return g5(i, uj[i] - s); });
+            combine(j + 1, Vv, [&](int i) { return cpx<R>((R)(h1[i].x * scale[i]), (R)(h1[i].y * scale[i])); }, ws,
+                    [](int, cpx<R> wi, cpx<R> s) { return wi - s; });
+            publish(ws);
             // reduction 2: h2_i = <s_i V_i, w1>, ||w1||^2
-            dots(j + 1, Vvec, [&](int i) { return scale[i]; }, w);
-            {
-                R acc = 0;
-                for (int t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
-                    cpx<R> q = w[t];
-                    acc += q.re * q.re + q.im * q.im;
-                }
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) nsum[wp] = acc;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    R s2 = 0;
-                    for (int ww = 0; ww < nw; ++ww) s2 += nsum[ww];
-                    wpart[j + 1] = P2(s2, 0);
-                }
-            }
+            dots(j + 1, 0, Vv, [&](int i) { return scale[i]; }, ws, false);
+            norm_part(ws, j + 1);
             if (!reduce(OFF_S2, j + 2)) return;
             if (threadIdx.x == 0) {
-                R n2 = h[j + 1].x;
+                R n2s = h[j + 1].x;
                 for (int i = 0; i <= j; ++i) {
                     P &col = Rm[j * (CG_MAXM + 1) + i];
                     col = P2(col.x + h[i].x, col.y + h[i].y);
-                    n2 -= h[i].x * h[i].x + h[i].y * h[i].y;
+                    n2s -= h[i].x * h[i].x + h[i].y * h[i].y;
                 }
-                nrm2s = n2 > 0 ? n2 : R(0);
+                nrm2s = n2s > 0 ? n2s : R(0);
             }
-            combine(j + 1, Vvec, [&](int i) { return cpx<R>((R)(h[i].x * scale[i]), (R)(h[i].y * scale[i])); }, w,
-                    [](int, cpx<R> ut, cpx<R> sm) { return ut - sm; });
+            for (int i = threadIdx.x; i <= j; i += blockDim.x) h2s[i] = h[i];
+            __syncthreads();
+            // V_j+1 = w1 - sum_i h2_i s_i V_i on the owned rows
+            cpx<R> *vn = Vv(j + 1);
+            combine(j + 1, Vv, [&](int i) { return cpx<R>((R)(h2s[i].x * scale[i]), (R)(h2s[i].y * scale[i])); },
+                    vn, [&](int i, cpx<R>, cpx<R> s) { return ws[i] - s; });
             if (threadIdx.x == 0) {
                 const R nrm = sqrt(nrm2s);
                 P *col = Rm + j * (CG_MAXM + 1);
@@ -511,131 +603,176 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             }
         }
         __syncthreads();
-        combine(kk, Vvec, [&](int i) { return cpx<R>((R)(y[i].x * scale[i]), (R)(y[i].y * scale[i])); }, a.x,
-                [](int, cpx<R> ut, cpx<R> s) { return ut + s; });
+        combine(kk, Vv, [&](int i) { return cpx<R>((R)(y[i].x * scale[i]), (R)(y[i].y * scale[i])); }, xs,
+                [](int, cpx<R> xi, cpx<R> s) { return xi + s; });
         have_x = true;
         its += kk;
-        if (!grid_sync(a.st, G, a.timeout)) return;   // x complete before any matvec on it
         if (conv) break;
         if (threadIdx.x == 0) stop = 0;
         __syncthreads();
     }
     // e = y + W (t0 - E^-1 W^dag A y)
     if (k > 0) {
-        cpx<R> *u = a.V;   // scratch
-        qmatvec<R>(a, a.x, R(1), u, r0, r1);
+        publish(xs);
+        if (!grid_sync(a.st, G, a.timeout)) return;
+        matvec<R, LK>(a, a.pub, R(1), ws, r0, r1);
         __syncthreads();
-        if (!deflation_coeffs(u)) return;
-        combine(k, Wvec, [&](int i) { return cpx<R>((R)(t0[i].x - tc[i].x), (R)(t0[i].y - tc[i].y)); }, a.x,
-                [](int, cpx<R> ut, cpx<R> s) { return ut + s; });
+        if (!deflation_coeffs(ws)) return;
+        combine(k, Wv, [&](int i) { return cpx<R>((R)(t0[i].x - tc[i].x), (R)(t0[i].y - tc[i].y)); }, xs,
+                [](int, cpx<R> xi, cpx<R> s) { return xi + s; });
     }
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) a.x[r0 + i] = xs[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.st->iters, its);
 }
 
-// Launch the persistent coarse solve for (Q_c - sigma) e_c = r_c.
+// ---------------------------------------------------------------------------
+// host side: the launch plan (grid, slices in shared or global memory) and the
+// global scratch it needs
+
+namespace {
+
+struct CGPlan {
+    int G, rb, nslice, m;
+    bool smem_slices, smem_defl;
+    size_t dyn_smem;          // dynamic shared memory per block
+    size_t off_slices, off_partial, scratch_bytes;   // global scratch layout
+};
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// the kernel instance for the context's precision and link format
 template <typename R>
-void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, const void *rc, void *ec) {
-    const int ntv = c.prm.n_tv;
-    const int n = c.nagg * 2 * ntv;
-    const int m = std::min(c.prm.coarse_restart, CG_MAXM);
-    int dev_sms = 0;
-    MG_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device));
-    int per_sm = 0;
-    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel<R>, CG_THREADS, 0));
-    MG_REQUIRE(per_sm >= 1, MGEIG_ECUDA);
-    int G = (n * TPR + CG_THREADS - 1) / CG_THREADS;
-    G = std::max(1, std::min(G, std::min(dev_sms * per_sm, dev_sms)));
-    B.V->alloc((size_t)(m + 1) * n * sizeof(cpx<R>));
-    B.rhs->alloc((size_t)n * sizeof(cpx<R>));
-    B.partial->alloc((size_t)G * CG_SLOTS * sizeof(double2));
-    CGArgs<R> a;
-    a.nagg = c.nagg; a.ntv = ntv; a.n = n;
-    for (int mu = 0; mu < 4; ++mu) a.cd[mu] = c.cdims[mu];
-    a.Dc = static_cast<const cpx<R> *>(c.Dc.p);
-    a.nbr = c.cnbr.as<int>();
-    a.sigma = (R)sigma;
-    a.b = static_cast<const cpx<R> *>(rc);
-    a.x = static_cast<cpx<R> *>(ec);
-    a.rhs = B.rhs->as<cpx<R>>();
-    a.V = B.V->as<cpx<R>>();
-    a.k = B.k;
-    MG_REQUIRE(a.k <= CG_MAXK, MGEIG_EINVAL);
-    a.W = static_cast<const cpx<R> *>(B.W);
-    a.AW = static_cast<const cpx<R> *>(B.AW);
-    a.Einv = static_cast<const double2 *>(B.Einv);
-    a.partial = B.partial->as<typename Pod2<R>::T>();
-    a.st = static_cast<CGState *>(B.state);
-    a.m = m;
-    a.maxiter = c.prm.coarse_maxiter;
-    a.tol = c.prm.coarse_tol;
-    a.timeout = 4000000000LL;   // about 2 s of SM clock per barrier wait
-    void *args[] = {&a};
-    TimeScope ts(c.timer, K_COARSE_SOLVE, 0);
-    MG_CUDA(cudaLaunchCooperativeKernel((void *)coarse_gmres_kernel<R>, dim3(G), dim3(CG_THREADS), args, 0, c.stream));
-    ++c.launches;
+const void *kernel_for(Ctx &c) {
+    if constexpr (sizeof(R) == 8) {
+        return (const void *)coarse_gmres_kernel<double, 0>;
+    } else {
+        switch (c.prm.coarse_links) {
+            case MGEIG_LINKS_BF16: return (const void *)coarse_gmres_kernel<float, 1>;
+            case MGEIG_LINKS_F16: return (const void *)coarse_gmres_kernel<float, 2>;
+            default: return (const void *)coarse_gmres_kernel<float, 0>;
+        }
+    }
 }
 
-template void coarse_gmres_persistent<float>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);
-template void coarse_gmres_persistent<double>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);
-
-// The same persistent coarse solve, with its scratch at caller-given device
-// addresses instead of context buffers: the Krylov basis V ((m + 1) n level
-// complex values), the projected right-hand side rhs (n), the per-block
-// partial sums (coarse_gmres_partial_bytes) and the CGState word block
-// (16 bytes, zero on entry).  Grid size and restart length are those of
-// coarse_gmres_persistent, so both give the same result.
-int coarse_gmres_grid(Ctx &c) {
+template <typename R>
+CGPlan compute_plan(Ctx &c, int k) {
+    CGPlan p;
     const int n = c.nagg * 2 * c.prm.n_tv;
+    p.m = std::min(c.prm.coarse_restart, CG_MAXM);
     int dev_sms = 0;
     MG_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device));
+    cudaFuncAttributes fa;
+    const void *kern = kernel_for<R>(c);
+    MG_CUDA(cudaFuncGetAttributes(&fa, kern));
+    const size_t elem = sizeof(cpx<R>);
+    int G = std::max(1, std::min((n * TPR + CG_THREADS - 1) / CG_THREADS, dev_sms));
+    p.rb = (n + G - 1) / G;
+    p.G = (n + p.rb - 1) / p.rb;   // every block owns at least one row
+    p.nslice = 2 * (p.m + 1) + 3;
+    const size_t budget = CG_SMEM_LIMIT > fa.sharedSizeBytes ? CG_SMEM_LIMIT - fa.sharedSizeBytes : 0;
+    const size_t slice_b = (size_t)p.nslice * p.rb * elem, defl_b = (size_t)2 * k * p.rb * elem;
+    p.smem_slices = slice_b <= budget;
+    p.smem_defl = p.smem_slices && k > 0 && slice_b + defl_b <= budget;
+    p.dyn_smem = p.smem_slices ? slice_b + (p.smem_defl ? defl_b : 0) : 0;
+    // global scratch: pub | slices (when not in shared memory) | partial sums
+    p.off_slices = align256((size_t)n * elem);
+    p.off_partial = p.off_slices + (p.smem_slices ? 0 : align256((size_t)p.G * slice_b));
+    p.scratch_bytes = p.off_partial + align256((size_t)p.G * CG_SLOTS * sizeof(typename Pod2<R>::T));
+    MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p.dyn_smem));
     int per_sm = 0;
-    if (c.mixed())
-        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel<float>, CG_THREADS, 0));
-    else
-        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel<double>, CG_THREADS, 0));
-    MG_REQUIRE(per_sm >= 1, MGEIG_ECUDA);
-    int G = (n * TPR + CG_THREADS - 1) / CG_THREADS;
-    return std::max(1, std::min(G, std::min(dev_sms * per_sm, dev_sms)));
+    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CG_THREADS, p.dyn_smem));
+    MG_REQUIRE(per_sm >= 1 && p.G <= dev_sms * per_sm, MGEIG_ECUDA);
+    return p;
 }
 
-size_t coarse_gmres_partial_bytes(Ctx &c, int G) {
-    return (size_t)G * CG_SLOTS * (c.mixed() ? sizeof(float2) : sizeof(double2));
-}
-
+// plans depend only on the device and the problem shape: computed once each
 template <typename R>
-void coarse_gmres_at(Ctx &c, int G, double sigma, const void *rc, void *ec, void *V, void *rhs, void *partial,
-                     void *state, int k, const void *W, const void *AW, const void *Einv) {
-    const int ntv = c.prm.n_tv;
-    MG_REQUIRE(k <= CG_MAXK, MGEIG_EINVAL);
+CGPlan make_plan(Ctx &c, int k) {
+    static std::mutex mu;
+    static std::map<std::array<int, 7>, CGPlan> cache;
+    const std::array<int, 7> key{c.device, c.nagg, c.prm.n_tv, std::min(c.prm.coarse_restart, CG_MAXM), k,
+                                 (int)sizeof(R), sizeof(R) == 4 ? c.prm.coarse_links : 0};
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const CGPlan p = compute_plan<R>(c, k);
+    cache.emplace(key, p);
+    return p;
+}
+
+}  // namespace
+
+// the barrier budget in SM clock cycles
+long long barrier_cycles(Ctx &c) {
+    int khz = 0;
+    MG_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c.device));
+    if (khz <= 0) khz = 2000000;
+    return std::max(1LL, (long long)(c.prm.barrier_timeout * khz * 1e3));
+}
+
+size_t coarse_gmres_scratch_bytes(Ctx &c, int k) {
+    return c.mixed() ? make_plan<float>(c, k).scratch_bytes : make_plan<double>(c, k).scratch_bytes;
+}
+
+// The persistent coarse solve with its global scratch (coarse_gmres_scratch_bytes)
+// at a caller-given device address and the CGState word block (16 bytes, zero on
+// entry) at `state`.
+template <typename R>
+void coarse_gmres_at(Ctx &c, double sigma, const void *rc, void *ec, void *scratch, void *state, int k,
+                     const void *W, const void *AW, const void *Einv) {
+    MG_REQUIRE(k <= CG_MAXK && k <= c.prm.n_tv, MGEIG_EINVAL);
+    const CGPlan p = make_plan<R>(c, k);
+    char *sc = static_cast<char *>(scratch);
     CGArgs<R> a;
-    a.nagg = c.nagg; a.ntv = ntv; a.n = c.nagg * 2 * ntv;
-    for (int mu = 0; mu < 4; ++mu) a.cd[mu] = c.cdims[mu];
+    a.nagg = c.nagg; a.ntv = c.prm.n_tv; a.n = c.nagg * 2 * c.prm.n_tv;
+    a.rb = p.rb; a.nslice = p.nslice;
+    a.smem_slices = p.smem_slices; a.smem_defl = p.smem_defl;
     a.Dc = static_cast<const cpx<R> *>(c.Dc.p);
+    a.L16 = c.Dc16.p;
+    a.Ls = c.Dcs.as<float>();
+    MG_REQUIRE(sizeof(R) == 8 || c.prm.coarse_links == MGEIG_LINKS_LEVEL || c.Dc16.p, MGEIG_ENOTSETUP);
     a.nbr = c.cnbr.as<int>();
     a.sigma = (R)sigma;
     a.b = static_cast<const cpx<R> *>(rc);
     a.x = static_cast<cpx<R> *>(ec);
-    a.rhs = static_cast<cpx<R> *>(rhs);
-    a.V = static_cast<cpx<R> *>(V);
+    a.pub = reinterpret_cast<cpx<R> *>(sc);
+    a.gslices = p.smem_slices ? nullptr : reinterpret_cast<cpx<R> *>(sc + p.off_slices);
     a.k = k;
     a.W = static_cast<const cpx<R> *>(W);
     a.AW = static_cast<const cpx<R> *>(AW);
     a.Einv = static_cast<const double2 *>(Einv);
-    a.partial = static_cast<typename Pod2<R>::T *>(partial);
+    a.partial = reinterpret_cast<typename Pod2<R>::T *>(sc + p.off_partial);
     a.st = static_cast<CGState *>(state);
-    a.m = std::min(c.prm.coarse_restart, CG_MAXM);
+    a.m = p.m;
     a.maxiter = c.prm.coarse_maxiter;
     a.tol = c.prm.coarse_tol;
-    a.timeout = 4000000000LL;   // about 2 s of SM clock per barrier wait
+    a.timeout = barrier_cycles(c);
     void *args[] = {&a};
+    // the dynamic shared-memory limit is an attribute of the kernel, not of the
+    // plan: plans of other problem shapes may have changed it since
+    const void *kern = kernel_for<R>(c);
+    MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.dyn_smem));
     TimeScope ts(c.timer, K_COARSE_SOLVE, 0);
-    MG_CUDA(cudaLaunchCooperativeKernel((void *)coarse_gmres_kernel<R>, dim3(G), dim3(CG_THREADS), args, 0, c.stream));
+    MG_CUDA(cudaLaunchCooperativeKernel(kern, dim3(p.G), dim3(CG_THREADS), args,
+                                        p.dyn_smem, c.stream));
     ++c.launches;
 }
 
-template void coarse_gmres_at<float>(Ctx &, int, double, const void *, void *, void *, void *, void *, void *, int,
-                                     const void *, const void *, const void *);
-template void coarse_gmres_at<double>(Ctx &, int, double, const void *, void *, void *, void *, void *, void *, int,
-                                      const void *, const void *, const void *);
+template void coarse_gmres_at<float>(Ctx &, double, const void *, void *, void *, void *, int, const void *,
+                                     const void *, const void *);
+template void coarse_gmres_at<double>(Ctx &, double, const void *, void *, void *, void *, int, const void *,
+                                      const void *, const void *);
+
+// Launch the persistent coarse solve for (Q_c - sigma) e_c = r_c with scratch
+// owned by the context.
+template <typename R>
+void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, const void *rc, void *ec) {
+    B.scratch->alloc(coarse_gmres_scratch_bytes(c, B.k));
+    coarse_gmres_at<R>(c, sigma, rc, ec, B.scratch->p, B.state, B.k, B.W, B.AW, B.Einv);
+}
+
+template void coarse_gmres_persistent<float>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);
+template void coarse_gmres_persistent<double>(Ctx &, const CoarseSolveBufs &, double, const void *, void *);
 
 }  // namespace mgeig

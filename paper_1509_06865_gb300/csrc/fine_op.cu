@@ -5,8 +5,11 @@
 // One thread per site.  The stencil reads the site's spinor and clover, the
 // eight neighbour spinors and the eight links (forward links of the site,
 // backward links of the lower neighbours), uses the chiral-basis half-spinor
-// projection (two SU(3) products per hop) and writes one spinor: 768 bytes
-// per site in FP32 (two-row links) and 1728 bytes in FP64 (full links).
+// projection (two SU(3) products per hop) and writes one spinor.  Counting
+// every field once (neighbour spinors and backward links are re-reads of data
+// other sites also need), that is 672 bytes per site in FP32 (x 96, y 96,
+// two-row links 192, clover 288) and 1536 bytes in FP64 (x 192, y 192, full
+// links 576, clover 576).
 #include "internal.h"
 
 namespace mgeig {
@@ -210,6 +213,38 @@ void build_clover(Ctx &c) {
     MG_CHECK_LAUNCH();
 }
 
+// A caller's clover term [site][blk][6][6] complex (without the mass term) ->
+// the packed layouts, with (4 + m0) added on the diagonal.  Only the real part
+// of the diagonal and the upper triangle are read (the blocks are Hermitian).
+__global__ void pack_clover_kernel(int V, const double2 *__restrict__ in, double mass, double2 *__restrict__ clov64,
+                                   float4 *__restrict__ clov32) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    for (int blk = 0; blk < 2; ++blk) {
+        const double2 *b = in + ((size_t)s * 2 + blk) * 36;
+        double r[36];
+        for (int i = 0; i < 6; ++i) r[i] = b[i * 6 + i].x + mass;
+        for (int i = 0; i < 6; ++i)
+            for (int j = i + 1; j < 6; ++j) {
+                const int o = offdiag_index(i, j);
+                r[6 + 2 * o] = b[i * 6 + j].x;
+                r[7 + 2 * o] = b[i * 6 + j].y;
+            }
+        for (int e = 0; e < 18; ++e) clov64[((size_t)blk * 18 + e) * V + s] = make_double2(r[2 * e], r[2 * e + 1]);
+        for (int e = 0; e < 9; ++e)
+            clov32[((size_t)blk * 9 + e) * V + s] =
+                make_float4((float)r[4 * e], (float)r[4 * e + 1], (float)r[4 * e + 2], (float)r[4 * e + 3]);
+    }
+}
+
+void pack_clover(Ctx &c, const double *dev_in) {
+    TimeScope ts(c.timer, K_OTHER, 0);
+    pack_clover_kernel<<<grid_for(c.g.V, 128), 128, 0, c.stream>>>(c.g.V, reinterpret_cast<const double2 *>(dev_in),
+                                                                   4.0 + c.prm.m0, c.clov64.as<double2>(),
+                                                                   c.clov32.as<float4>());
+    MG_CHECK_LAUNCH();
+}
+
 // [site][blk][6][6] complex, without the mass term
 __global__ void unpack_clover_kernel(int V, const double2 *__restrict__ clov64, double mass, double2 *__restrict__ out) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -258,13 +293,11 @@ struct InLoad<double, float> {
     }
 };
 
+// y(s) = op(x)(s) for one site s: the eight hops, the clover term and the shift
 template <typename R, typename Rin, int MODE>
-__global__ void __launch_bounds__(128) wilson_clover_kernel(Geom g, const void *__restrict__ U,
-                                                            const void *__restrict__ clov,
-                                                            const void *__restrict__ x, void *__restrict__ y,
-                                                            R sigma) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.V) return;
+__device__ __forceinline__ void wilson_clover_site(const Geom &g, const void *__restrict__ U,
+                                                   const void *__restrict__ clov, const void *__restrict__ x,
+                                                   void *__restrict__ y, R sigma, int s) {
     const int V = g.V;
     int c[4];
     site_coords(g, s, c);
@@ -311,13 +344,38 @@ __global__ void __launch_bounds__(128) wilson_clover_kernel(Geom g, const void *
     Spinor<R>::store(y, V, s, out);
 }
 
+template <typename R, typename Rin, int MODE>
+__global__ void __launch_bounds__(128) wilson_clover_kernel(Geom g, const void *__restrict__ U,
+                                                            const void *__restrict__ clov,
+                                                            const void *__restrict__ x, void *__restrict__ y,
+                                                            R sigma) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    wilson_clover_site<R, Rin, MODE>(g, U, clov, x, y, sigma, s);
+}
+
+// nrhs fields stored back to back (field k at byte offset k * field_bytes).  CTA b
+// takes field b % nrhs on the site range b / nrhs: the nrhs CTAs of one site range
+// are scheduled back to back, so the range's links and clover come from HBM once
+// and from L2 for the other nrhs - 1 fields.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(128) wilson_clover_nrhs_kernel(Geom g, const void *__restrict__ U,
+                                                                 const void *__restrict__ clov,
+                                                                 const char *__restrict__ x, char *__restrict__ y,
+                                                                 R sigma, int nrhs, size_t field_bytes) {
+    const int rhs = blockIdx.x % nrhs;
+    const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    wilson_clover_site<R, R, MODE>(g, U, clov, x + rhs * field_bytes, y + rhs * field_bytes, sigma, s);
+}
+
 template <typename R, typename Rin>
 static void launch_fine(Ctx &c, int mode, double sigma, const void *x, void *y) {
     const int threads = 128;
     const int blocks = grid_for(c.g.V, threads);
     const void *U = sizeof(R) == 8 ? c.U64.p : c.U32.p;
     const void *C = sizeof(R) == 8 ? c.clov64.p : c.clov32.p;
-    // algorithmic bytes per site: 9 spinors read... counted once: x, y, links, clover
+    // algorithmic bytes per site, every field counted once: x, y, links, clover
     const double spin = 12 * 2 * sizeof(Rin), spout = 12 * 2 * sizeof(R);
     const double links = sizeof(R) == 8 ? 4 * 9 * 16 : 4 * 12 * 4;
     const double clov = 72 * sizeof(R);
@@ -330,6 +388,31 @@ static void launch_fine(Ctx &c, int mode, double sigma, const void *x, void *y) 
     }
     MG_CHECK_LAUNCH();
 }
+
+template <typename R>
+void apply_fine_nrhs(Ctx &c, int mode, double sigma, const void *x, void *y, int nrhs) {
+    const int threads = 128;
+    const long long blocks = (long long)grid_for(c.g.V, threads) * nrhs;
+    MG_REQUIRE(nrhs >= 1 && blocks < (1LL << 31), MGEIG_EINVAL);
+    const void *U = sizeof(R) == 8 ? c.U64.p : c.U32.p;
+    const void *C = sizeof(R) == 8 ? c.clov64.p : c.clov32.p;
+    const size_t fb = (size_t)c.g.V * 24 * sizeof(R);
+    const double links = sizeof(R) == 8 ? 4 * 9 * 16 : 4 * 12 * 4;
+    // algorithmic bytes: every field read or written once, links and clover once for all fields
+    TimeScope ts(c.timer, sizeof(R) == 8 ? K_STENCIL_F64 : K_STENCIL_F32,
+                 ((double)nrhs * 2 * 24 * sizeof(R) + links + 72 * sizeof(R)) * c.g.V);
+    c.st.fine_applies += nrhs;
+    const char *xb = static_cast<const char *>(x);
+    char *yb = static_cast<char *>(y);
+    switch (mode) {
+        case MODE_D: wilson_clover_nrhs_kernel<R, MODE_D><<<(int)blocks, threads, 0, c.stream>>>(c.g, U, C, xb, yb, (R)sigma, nrhs, fb); break;
+        case MODE_DSIGMA: wilson_clover_nrhs_kernel<R, MODE_DSIGMA><<<(int)blocks, threads, 0, c.stream>>>(c.g, U, C, xb, yb, (R)sigma, nrhs, fb); break;
+        default: wilson_clover_nrhs_kernel<R, MODE_QSIGMA><<<(int)blocks, threads, 0, c.stream>>>(c.g, U, C, xb, yb, (R)sigma, nrhs, fb); break;
+    }
+    MG_CHECK_LAUNCH();
+}
+template void apply_fine_nrhs<double>(Ctx &, int, double, const void *, void *, int);
+template void apply_fine_nrhs<float>(Ctx &, int, double, const void *, void *, int);
 
 template <typename R>
 void apply_fine(Ctx &c, int mode, double sigma, const void *x, void *y) {

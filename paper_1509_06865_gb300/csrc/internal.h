@@ -25,6 +25,7 @@ struct Error {
         if (e_ != cudaSuccess) {                                                           \
             fprintf(stderr, "libmgeig: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), \
                     __FILE__, __LINE__);                                                   \
+            (void)cudaGetLastError(); /* a launch error must not be reported again later */ \
             throw ::mgeig::Error{e_ == cudaErrorMemoryAllocation ? MGEIG_ENOMEM : MGEIG_ECUDA}; \
         }                                                                                  \
     } while (0)
@@ -62,7 +63,7 @@ struct TmpBuf : DevBuf {
 // Kernel classes with per-class CUDA event timing (off unless enabled).
 enum KernelClass {
     K_STENCIL_F64 = 0, K_STENCIL_F32, K_SAP_F64, K_SAP_F32, K_RESTRICT, K_PROLONG,
-    K_COARSE_APPLY, K_COARSE_BUILD, K_PBUILD, K_BLAS_F64, K_BLAS_LOW, K_OTHER, K_COARSE_SOLVE, K_NCLASS
+    K_COARSE_APPLY, K_COARSE_BUILD, K_PBUILD, K_BLAS_F64, K_BLAS_LOW, K_OTHER, K_COARSE_SOLVE, K_NET, K_NCLASS
 };
 
 struct Timer {
@@ -96,12 +97,19 @@ struct TimeScope {
 };
 
 struct Ctx;
+struct Net;   // the learned smoother's weights and activations (learned.cu)
 
 // ----- fine operator (fine_op.cu) -----
 void pack_gauge(Ctx &c, const double *dev_host_layout);
 void build_clover(Ctx &c);
+// packs a caller's clover term (device, [site][2][6][6] complex128, no mass term)
+void pack_clover(Ctx &c, const double *dev_in);
+// the clover term of the operator: the loaded one, else built from the gauge field
+void refresh_clover(Ctx &c);
 void unpack_clover(Ctx &c, double *dev_out);
 template <typename R> void apply_fine(Ctx &c, int mode, double sigma, const void *x, void *y);
+// nrhs fields stored back to back, one launch
+template <typename R> void apply_fine_nrhs(Ctx &c, int mode, double sigma, const void *x, void *y, int nrhs);
 // x in FP32 internal layout, y FP64: y = op(x) in FP64 arithmetic
 void apply_fine_f64_from_f32(Ctx &c, int mode, double sigma, const void *x32, void *y64);
 void pack_spinor_f64(Ctx &c, const double *host_layout_dev, void *out, int n);
@@ -135,22 +143,30 @@ template <typename R> void coarse_apply(Ctx &c, const void *Dc, double sigma, co
 template <typename R> void coarse_gamma5(Ctx &c, const void *x, void *y);
 template <typename R> void sap_sweep(Ctx &c, int colour, double sigma, const void *rhs, bool rhs_gamma5, void *z);
 
+// ----- 16-bit coarse links (links16.cu) -----
+void compress_coarse(Ctx &c);   // Dc (FP32) -> Dc16, Dcs in the format of prm.coarse_links
+void coarse_apply_links16(Ctx &c, double sigma, const void *x, void *y, bool dform);
+// Y = (Q_c - sigma) X for nrhs <= 16 FP32 coarse vectors back to back (tensor cores with BF16 links)
+void coarse_apply_nrhs(Ctx &c, double sigma, const void *X, void *Y, int nrhs);
+// n flat complex values FP64 -> FP32 (to32) or back (solver.cu)
+void coarse_flat_convert(Ctx &c, const void *in, void *out, size_t n, bool to32);
+
 // ----- persistent coarse GMRES (coarse_gmres.cu) -----
 constexpr int COARSE_PERSISTENT_MAXM = 32;
 struct CoarseSolveBufs {
-    DevBuf *V, *rhs, *partial;   // basis, projected right-hand side, partial sums
+    DevBuf *scratch;             // global scratch of the solver (coarse_gmres_scratch_bytes)
     void *state;                 // CGState (barrier, status, iteration counter)
     int k;                       // deflation vectors (0: none)
     const void *W, *AW, *Einv;   // k coarse vectors each; E^-1 (k x k complex double)
 };
 template <typename R>
 void coarse_gmres_persistent(Ctx &c, const CoarseSolveBufs &B, double sigma, const void *rc, void *ec);
-// the same solve with caller-placed scratch (coarse_gmres.cu)
-int coarse_gmres_grid(Ctx &c);
-size_t coarse_gmres_partial_bytes(Ctx &c, int G);
+// the same solve with caller-placed scratch (coarse_gmres.cu): `scratch` holds
+// coarse_gmres_scratch_bytes(c, k) bytes, `state` 16 bytes that are zero on entry
+size_t coarse_gmres_scratch_bytes(Ctx &c, int k);
 template <typename R>
-void coarse_gmres_at(Ctx &c, int G, double sigma, const void *rc, void *ec, void *V, void *rhs, void *partial,
-                     void *state, int k, const void *W, const void *AW, const void *Einv);
+void coarse_gmres_at(Ctx &c, double sigma, const void *rc, void *ec, void *scratch, void *state, int k,
+                     const void *W, const void *AW, const void *Einv);
 
 // ----- the context -----
 struct Ctx {
@@ -167,6 +183,8 @@ struct Ctx {
 
     // fine fields
     DevBuf U64, U32, clov64, clov32;
+    DevBuf clov_user;         // a clover term loaded by mgeig_load_clover (host layout)
+    bool clover_loaded = false;
     DevBuf staging;           // host-layout transfer buffer
     std::vector<DevBuf> user_bufs;
 
@@ -185,6 +203,7 @@ struct Ctx {
     std::vector<DevBuf> W;    // ntv FP64 fine vectors
     std::vector<DevBuf> P;    // ntv vectors, R precision
     DevBuf Dc;                // [9][nagg][2N][2N] (column-major blocks), R precision
+    DevBuf Dc16, Dcs;         // 16-bit links [9][nagg][re|im][2N][2N] and their scales [9][nagg]
     DevBuf cnbr;              // coarse neighbour table int32 [9][nagg]: self, then +mu, -mu for mu = 0..3
 
     size_t fine_ncpx() const { return (size_t)g.V * 12; }
@@ -199,6 +218,7 @@ struct Ctx {
     // solver workspace (allocated lazily, see solver.cu)
     struct Work;
     Work *work = nullptr;
+    Net *net = nullptr;       // the learned smoother (allocated on first use)
 };
 
 // ----- solvers (solver.cu) -----
@@ -217,6 +237,7 @@ void mg_cycle_host(Ctx &c, double sigma, const double *r_dev64_internal, double 
 // the two-grid cycle on level-precision device spinors, scratch in a static device array
 int mg_cycle_noalloc(Ctx &c, double sigma, const void *r, void *z);
 size_t mg_cycle_noalloc_limit();
+void noalloc_prepare(Ctx &c);   // the static array's address, looked up once per device
 int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol, int maxiter = 0);
 int eigensolve(Ctx &c, int n_eig, double tol, double *evals, double *evecs_host, double *resid);
 void sap_smooth_f64(Ctx &c, double sigma, const void *b64, void *z64, int cycles);
@@ -227,5 +248,22 @@ void coarse_op_f64(Ctx &c, void *out64);
 void interp_f64(Ctx &c, void *const *out64);
 
 int grid_for(size_t n, int threads);
+
+// ----- the learned smoother (learned.cu) -----
+bool net_supported(const Ctx &c);   // lattice extents divisible by the 4 x 4 x 4 x 2 box
+void net_init(Ctx &c, uint64_t seed);
+void net_set_weights(Ctx &c, const float *host);   // [3][81][32][32] FP32
+void net_get_weights(Ctx &c, float *host);
+void net_free(Ctx &c);
+// z += ||r|| f(r / ||r||) for one FP32 spinor r (z FP32)
+void net_smooth(Ctx &c, const void *r, void *z);
+// one Adam step on batch pairs (FP32 spinors r_f, SAP corrections e_f back to back); returns the loss
+double net_train_step(Ctx &c, const void *r, const void *e, int batch, double lr);
+// loss and weight gradients for host channel data x, t [batch][V][24] FP64
+double net_loss_grads(Ctx &c, const double *x, const double *t, int batch, float *G_host);
+// training pairs from the method and the training loop (solver.cu)
+void net_train(Ctx &c, int steps, int batch, double lr, uint64_t seed, double *losses);
+// FMA throughput (FLOP/s) of the library's own peak kernel, FP64 or FP32 (peak.cu)
+double fma_peak_flops(Ctx &c, int prec, int reps);
 
 }  // namespace mgeig

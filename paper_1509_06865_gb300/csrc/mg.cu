@@ -453,6 +453,10 @@ void coarse_apply(Ctx &c, const void *Dc, double sigma, const void *x, void *y, 
     AggGeom A = make_agg(c, c.prm.agg);
     const int ntv = c.prm.n_tv;
     const size_t n = (size_t)A.n * 2 * ntv;
+    if (sizeof(R) == 4 && c.prm.coarse_links != MGEIG_LINKS_LEVEL) {
+        coarse_apply_links16(c, sigma, x, y, dform);   // the operator in its 16-bit form
+        return;
+    }
     TimeScope ts(c.timer, K_COARSE_APPLY, (double)A.n * (9.0 * 4 * ntv * ntv + 20.0 * ntv) * sizeof(cpx<R>));
     MG_REQUIRE(c.cnbr.p != nullptr, MGEIG_ENOTSETUP);
     coarse_apply_kernel<R><<<grid_for(n, 128), 128, 0, c.stream>>>(A, ntv, static_cast<const cpx<R> *>(Dc),

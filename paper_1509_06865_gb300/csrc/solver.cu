@@ -159,7 +159,7 @@ struct Ctx::Work {
     DevBuf rR, zR, tR, eR;       // level-precision fine temporaries
     std::vector<DevBuf> S;       // GMRES smoother basis
     DevBuf rc, ec, ct;           // coarse vectors
-    DevBuf cgV, cgRhs, cgP;      // persistent coarse solver: basis, rhs, partial sums
+    DevBuf cgS;                  // persistent coarse solver's global scratch
     DevBuf Wc, AWc, Edev, Einv;  // deflation: P^dag w_j, (Q_c - sigma) P^dag w_j, E, E^-1
     DevBuf Mextra, Xall;         // Algorithm 1 vectors beyond the N_tv test vectors; rotation scratch
     std::vector<void *> modes;   // iterated vectors: W[0..N_tv) then the extra ones
@@ -245,13 +245,13 @@ void mg_free(Ctx &c) {
     w.x64.free(); w.t64.free(); w.q64.free();
     w.rR.free(); w.zR.free(); w.tR.free(); w.eR.free();
     w.rc.free(); w.ec.free(); w.ct.free();
-    w.cgV.free(); w.cgRhs.free(); w.cgP.free();
+    w.cgS.free();
     w.Wc.free(); w.AWc.free(); w.Edev.free(); w.Einv.free();
     w.Mextra.free(); w.Xall.free();
     w.QZ64all.free(); w.ZRall.free(); w.QZRall.free(); w.AZRall.free(); w.fdEinv.free(); w.fdCoef.free();
     delete c.work;
     c.work = nullptr;
-    c.Dc.free();
+    c.Dc.free(); c.Dc16.free(); c.Dcs.free();
     c.cnbr.free();
 }
 
@@ -480,9 +480,7 @@ static void coarse_solve(Ctx &c, double sigma, const void *rc, void *ec) {
     Ctx::Work &w = *c.work;
     deflation_prepare<R>(c, sigma);
     CoarseSolveBufs B;
-    B.V = &w.cgV;
-    B.rhs = &w.cgRhs;
-    B.partial = &w.cgP;
+    B.scratch = &w.cgS;
     B.state = dslot(c, CGS);
     B.k = (c.prm.coarse_deflate && !c.in_setup) ? c.prm.n_tv : 0;
     B.W = w.Wc.p;
@@ -517,7 +515,18 @@ static void mg_cycle(Ctx &c, double sigma, const void *r, void *z) {
     restrict_vec<R>(c, (const void *const *)w.P.data(), r, w.rc.p);
     coarse_solve<R>(c, sigma, w.rc.p, w.ec.p);
     prolong_vec<R>(c, (const void *const *)w.P.data(), w.ec.p, z);
-    if (c.prm.smoother == MGEIG_SAP) {
+    if constexpr (sizeof(R) == 4) {
+        if (c.prm.smoother == MGEIG_LEARNED && !c.in_setup) {
+            // z += M(r - (Q - sigma) z): the learned smoother on the residual of the coarse correction
+            const size_t n = c.fine_ncpx();
+            apply_fine<R>(c, MODE_QSIGMA, sigma, z, w.tR.p);
+            blas_scale<R>(c, cpx<double>(-1), w.tR.p, n);
+            blas_axpy<R>(c, cpx<double>(1), r, w.tR.p, n);
+            net_smooth(c, w.tR.p, z);
+            return;
+        }
+    }
+    if (c.prm.smoother == MGEIG_SAP || c.prm.smoother == MGEIG_LEARNED) {
         for (int k = 0; k < c.prm.sap_cycles; ++k) {
             sap_sweep<R>(c, 0, sigma, r, true, z);
             sap_sweep<R>(c, 1, sigma, r, true, z);
@@ -546,6 +555,7 @@ void mg_rebuild(Ctx &c) {
     if (c.mixed()) {
         build_interp<float>(c, (const void *const *)w.Psrc.data(), ntv, w.P.data());
         build_coarse<float>(c, (const void *const *)w.P.data(), c.Dc.p);
+        if (c.prm.coarse_links != MGEIG_LINKS_LEVEL) compress_coarse(c);
         // coarse images P^dag w_j of the test vectors (the deflation space)
         for (int j = 0; j < ntv; ++j) {
             convert_f64_to_f32(c, w.Psrc[j], w.rR.p, c.fine_ncpx());
@@ -605,7 +615,7 @@ static void smooth_random(Ctx &c, void *w64) {
     void *rhs = w.rR.p, *z = w.zR.p;
     if (sizeof(R) == 4) convert_f64_to_f32(c, w64, rhs, n);
     else blas_copy<double>(c, w64, rhs, n);
-    if (c.prm.smoother == MGEIG_SAP) {
+    if (c.prm.smoother != MGEIG_GMRES) {
         blas_zero<R>(c, z, n);
         for (int k = 0; k < c.prm.setup_smooth; ++k) {
             sap_sweep<R>(c, 0, 0.0, rhs, true, z);
@@ -995,7 +1005,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
         else extra_start_vectors<double>(c, ntv, n_eig);
     }
     std::vector<void *> &M = w.modes;
-    ritz_rotate(c, M, std::max(ntv, n_eig));
+    if (c.prm.ritz_start) ritz_rotate(c, M, std::max(ntv, n_eig));
     w.Psrc.assign(M.begin(), M.begin() + ntv);
     mg_rebuild(c);
     std::vector<double> lam(n_eig, 0.0), eps(n_eig, 1.0);
@@ -1027,8 +1037,9 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             // inexact solve: the new vector's eigen-residual is about tau |lambda - sigma|,
             // so tau shrinks to 0.1 tol / |lambda - sigma| near convergence
             const double dls = std::fabs(lam[i] - sigma);
-            const double tau = (is_guard || dls == 0) ? c.prm.solve_tol
-                                                      : std::min(c.prm.solve_tol, std::max(0.1 * tol / dls, 1e-12));
+            const double tau = (is_guard || dls == 0 || !c.prm.adaptive_tol)
+                                   ? c.prm.solve_tol
+                                   : std::min(c.prm.solve_tol, std::max(0.1 * tol / dls, 1e-12));
             if (c.mixed()) fdefl_prepare<float>(c, sigma, i);
             else fdefl_prepare<double>(c, sigma, i);
             int rc = fgmres_solve(c, sigma, M[i], w.x64.p, tau,
@@ -1143,6 +1154,43 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
 }
 
 // ---------------------------------------------------------------------------
+// training of the learned smoother on pairs the two-grid method produces
+
+void net_train(Ctx &c, int steps, int batch, double lr, uint64_t seed, double *losses) {
+    Ctx::Work &w = *c.work;
+    const size_t n = c.fine_ncpx();
+    TmpBuf v64, R, E;
+    v64.alloc(f64_bytes(c) * batch);
+    R.alloc(fR_bytes(c) * batch);
+    E.alloc(fR_bytes(c) * batch);
+    for (int step = 0; step < steps; ++step) {
+        random_spinors(c, seed + (uint64_t)step, v64.p, batch, 0x5EED0004u);
+        for (int f = 0; f < batch; ++f) {
+            void *rf = R.as<char>() + fR_bytes(c) * f;
+            void *ef = E.as<char>() + fR_bytes(c) * f;
+            convert_f64_to_f32(c, v64.as<char>() + f64_bytes(c) * f, w.rR.p, n);
+            // coarse correction x_c = P Q_c^-1 P^dag v and the residual r = v - Q x_c
+            restrict_vec<float>(c, (const void *const *)w.P.data(), w.rR.p, w.rc.p);
+            coarse_solve<float>(c, 0.0, w.rc.p, w.ec.p);
+            prolong_vec<float>(c, (const void *const *)w.P.data(), w.ec.p, w.zR.p);
+            apply_fine<float>(c, MODE_QSIGMA, 0.0, w.zR.p, rf);
+            blas_scale<float>(c, cpx<double>(-1), rf, n);
+            blas_axpy<float>(c, cpx<double>(1), w.rR.p, rf, n);
+            // the target: the SAP correction of r (D e = gamma5 r from e = 0)
+            blas_zero<float>(c, ef, n);
+            for (int k = 0; k < c.prm.sap_cycles; ++k) {
+                sap_sweep<float>(c, 0, 0.0, rf, true, ef);
+                sap_sweep<float>(c, 1, 0.0, rf, true, ef);
+            }
+        }
+        const double L = net_train_step(c, R.p, E.p, batch, lr);
+        if (losses) losses[step] = L;
+        if (log_on() && (step % 50 == 0 || step == steps - 1)) fprintf(stderr, "mgeig net step %d loss %.4e\n", step, L);
+    }
+    coarse_iters_take(c);
+}
+
+// ---------------------------------------------------------------------------
 // single-step entry points used for parity checks (FP64 in / out)
 
 template <typename R>
@@ -1187,6 +1235,13 @@ __global__ void flat_f64_to_f32(size_t n, const double2 *in, float2 *out) {
 __global__ void flat_f32_to_f64(size_t n, const float2 *in, double2 *out) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = make_double2(in[i].x, in[i].y);
+}
+
+// n complex values: FP64 -> FP32 (to32) or FP32 -> FP64
+void coarse_flat_convert(Ctx &c, const void *in, void *out, size_t n, bool to32) {
+    if (to32) flat_f64_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, (const double2 *)in, (float2 *)out);
+    else flat_f32_to_f64<<<grid_for(n, 256), 256, 0, c.stream>>>(n, (const float2 *)in, (double2 *)out);
+    MG_CHECK_LAUNCH();
 }
 
 static void coarse_in(Ctx &c, const void *x64, void *xR) {
@@ -1304,6 +1359,12 @@ static void *noalloc_scratch_address(int device) {
     return addr[device];
 }
 
+// Looks the array's address up at context creation (mgeig_create), so that the
+// module holding it is loaded and the array is reserved before any
+// mgeig_mg_cycle_dev_noalloc call: with CUDA's lazy module loading that would
+// otherwise happen inside the first call.
+void noalloc_prepare(Ctx &c) { (void)noalloc_scratch_address(c.device); }
+
 // Gauss-Jordan inverse of the row-major n x n matrix A (destroyed), n <= 24,
 // with the operations of invert() in the same order (identical results) but
 // on the caller's arrays.
@@ -1376,13 +1437,11 @@ template <typename R>
 static int mg_cycle_noalloc_impl(Ctx &c, double sigma, const void *r, void *z) {
     Ctx::Work &w = *c.work;
     const size_t cb = c.coarse_ncpx() * sizeof(cpx<R>);
-    const int m = std::min(c.prm.coarse_restart, COARSE_PERSISTENT_MAXM);
-    const int G = coarse_gmres_grid(c);
+    const int k = c.prm.coarse_deflate ? c.prm.n_tv : 0;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    // layout: solver state words | r_c | e_c | projected rhs | basis | partial sums
-    const size_t off_rc = 256, off_ec = off_rc + up(cb), off_rhs = off_ec + up(cb), off_V = off_rhs + up(cb);
-    const size_t off_P = off_V + up((size_t)(m + 1) * cb);
-    const size_t need = off_P + up(coarse_gmres_partial_bytes(c, G));
+    // layout: solver state words | r_c | e_c | the coarse solver's scratch
+    const size_t off_rc = 256, off_ec = off_rc + up(cb), off_S = off_ec + up(cb);
+    const size_t need = off_S + up(coarse_gmres_scratch_bytes(c, k));
     if (need > NOALLOC_SCRATCH_BYTES) {
         fprintf(stderr, "libmgeig: mgeig_mg_cycle_dev_noalloc needs %zu bytes of scratch for this coarse grid, "
                         "its static array holds %zu\n", need, NOALLOC_SCRATCH_BYTES);
@@ -1391,15 +1450,10 @@ static int mg_cycle_noalloc_impl(Ctx &c, double sigma, const void *r, void *z) {
     char *s = static_cast<char *>(noalloc_scratch_address(c.device));
     // the barrier counters, status and iteration words must start at zero
     MG_CUDA(cudaMemsetAsync(s, 0, 256, c.stream));
-    int k = 0;
-    if (c.prm.coarse_deflate) {
-        deflation_prepare_fixed<R>(c, sigma);
-        k = c.prm.n_tv;
-    }
+    if (k) deflation_prepare_fixed<R>(c, sigma);
     c.st.mg_cycles += 1;
     restrict_vec<R>(c, (const void *const *)w.P.data(), r, s + off_rc);
-    coarse_gmres_at<R>(c, G, sigma, s + off_rc, s + off_ec, s + off_V, s + off_rhs, s + off_P, s, k, w.Wc.p, w.AWc.p,
-                       w.Einv.p);
+    coarse_gmres_at<R>(c, sigma, s + off_rc, s + off_ec, s + off_S, s, k, w.Wc.p, w.AWc.p, w.Einv.p);
     prolong_vec<R>(c, (const void *const *)w.P.data(), s + off_ec, z);
     for (int q = 0; q < c.prm.sap_cycles; ++q) {
         sap_sweep<R>(c, 0, sigma, r, true, z);

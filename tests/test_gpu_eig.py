@@ -32,8 +32,11 @@ def test_eigensolve_4x4x4x4_vs_dense(ref, precision, smoother):
     U, op, Qm, w, v = ref
     c = DENSE4
     ctx = Context(c["dims"])
+    # the GMRES smoother iterates 16 guard vectors: with the default 8 its FP64
+    # path converges to the 5th mode instead of the 3rd on this field (the miss
+    # noted after Algorithm 1); 16 give the full set in both precisions
     ctx.set_params(m0=c["m0"], csw=c["csw"], agg=(2, 2, 2, 2), n_tv=8, sap_block=(2, 2, 2, 2),
-                   precision=precision, smoother=smoother)
+                   precision=precision, smoother=smoother, n_guard=16 if smoother == 1 else -1)
     ctx.load_gauge(U)
     ctx.setup(c["seed"])
     lam, V, res, st = ctx.eigensolve(c["n_eig"], 1e-10)
@@ -46,15 +49,7 @@ def test_eigensolve_4x4x4x4_vs_dense(ref, precision, smoother):
         assert abs(np.linalg.norm(x) - 1) < 1e-12
         assert np.linalg.norm(Qm @ x - lam[i] * x) <= 1.05e-10
     want = w[:c["n_eig"]]
-    if smoother == 1:
-        # GMRES(k) smoother: every returned pair is an eigenpair of the dense Q and
-        # the two lowest are found; on this field Algorithm 1 with this weaker
-        # smoother converges to the 5th mode instead of the 3rd (the miss the
-        # paper notes after Algorithm 1), so the full set is not asserted.
-        full = np.linalg.eigvalsh(Qm)
-        assert all(np.min(np.abs(full - l)) <= 1e-10 * abs(l) for l in lam)
-        assert np.abs(lam[:2] - want[:2]).max() <= 1e-10 * np.abs(want).max()
-        return
+    # the full set of the 4 lowest, for both smoothers
     assert np.abs(lam - want).max() <= 1e-10 * np.abs(want).max()
     for i in range(c["n_eig"]):
         x = V[i].ravel()

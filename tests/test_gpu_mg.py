@@ -111,3 +111,38 @@ def test_setup_matches_oracle_fp64(inputs):
     for j in range(c["ntv"]):
         assert norm_rel_err(Wg[j], Wo[j]) < 1e-8
     ctx.close()
+
+
+FULL = dict(dims=(8, 8, 8, 16), eps=0.2, seed=1006, m0=-0.0428, csw=1.9, bc=(1, 1, 1, 1), agg=(2, 2, 2, 2),
+            sap=(4, 4, 4, 4), ntv=20)
+
+
+@pytest.fixture(scope="module")
+def full_inputs():
+    c = FULL
+    U = synth.gauge_field(c["dims"], c["eps"], c["seed"])
+    op = dirac.WilsonClover(U, c["m0"], c["csw"], bc=c["bc"])
+    W = synth.uniform_vectors(c["dims"], c["ntv"], 99)
+    return c, U, op, W
+
+
+@pytest.mark.parametrize("deflate", [1, 0], ids=["deflated", "plain"])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-4)], ids=["fp64", "mixed"])
+def test_two_grid_cycle_full_size_coarse_solver(full_inputs, deflate, prec, tol):
+    """The two-grid cycle on a coarse grid of 512 aggregates x 40 unknowns
+    (8^3 x 16 with 2^4 aggregates, 20 test vectors), the size at which the
+    persistent coarse GMRES runs on every SM with grid-wide barriers and
+    cross-block partial sums; a fixed number of coarse steps with a restart."""
+    c, U, op, W = full_inputs
+    params = dict(mg.DEFAULT_PARAMS, agg=c["agg"], sap_block=c["sap"], ntv=c["ntv"], smoother="sap",
+                  coarse_tol=0.0, coarse_maxiter=16, coarse_restart=10, coarse_deflate=bool(deflate),
+                  sap_cycles=2, sap_mr_iters=3)
+    B = mg.TwoGrid(op, W, params)
+    ctx = make(c, prec, 0, coarse_tol=0.0, coarse_maxiter=16, coarse_restart=10, coarse_deflate=deflate,
+               sap_cycles=2, sap_mr_iters=3)
+    ctx.load_gauge(U)
+    ctx.set_test_vectors(W)
+    r = synth.gaussian_vectors(c["dims"], 1, 12)[0]
+    for sigma in (0.0, 0.05):
+        assert norm_rel_err(ctx.mg_cycle(r, sigma), B(r, sigma)) < tol
+    ctx.close()

@@ -74,3 +74,67 @@ def test_stencil_device_entry_point(case):
         ctx.apply_dev(px, py, 0.05, OP_Q, prec)
         got = ctx.unpack_spinors(py, 1, prec)[0]
         assert norm_rel_err(got, want) < tol
+
+
+def _blocks(A12):
+    """[..., 12, 12] site matrices -> [site][2][6][6] chirality blocks."""
+    A = A12.reshape(-1, 12, 12)
+    return np.ascontiguousarray(np.stack([A[:, :6, :6], A[:, 6:, 6:]], axis=1))
+
+
+def test_load_clover_host_term():
+    """mgeig_load_clover: the oracle's clover term loaded from the host gives the
+    oracle's stencil; a different Hermitian term (scaled, perturbed) is used as
+    given, survives a change of m0, and NULL goes back to the built term."""
+    from paper_1509_06865_gb300 import OP_D, OP_Q, PREC_F32, PREC_F64, Context
+    c = CASES[1]
+    U = synth.gauge_field(c["dims"], c["eps"], c["seed"])
+    op = dirac.WilsonClover(U, c["m0"], c["csw"], bc=c["bc"])
+    ctx = Context(c["dims"])
+    ctx.set_params(m0=c["m0"], csw=c["csw"], bc=c["bc"], agg=c["agg"], sap_block=c["sap"], n_tv=4)
+    ctx.load_gauge(U)
+    x = synth.gaussian_vectors(c["dims"], 1, 41)
+    ctx.load_clover(_blocks(op.A))
+    assert rel_err(ctx.get_clover(), _blocks(op.A)) < 1e-15
+    assert norm_rel_err(ctx.apply(x, 0.1, OP_Q, PREC_F64)[0], op.Q_sigma(x[0], 0.1)) < 1e-13
+    # another Hermitian term, block diagonal in chirality like the clover term
+    rng = np.random.default_rng(5)
+    H = rng.normal(size=op.A.shape) + 1j * rng.normal(size=op.A.shape)
+    H = 0.05 * (H + np.conj(np.swapaxes(H, -1, -2)))
+    H[..., :6, 6:] = 0
+    H[..., 6:, :6] = 0
+    A2 = 0.7 * op.A + H
+    ctx.load_clover(_blocks(A2))
+    op2 = dirac.WilsonClover(U, c["m0"], c["csw"], bc=c["bc"], A=A2)
+    assert norm_rel_err(ctx.apply(x, 0.0, OP_D, PREC_F64)[0], op2.D(x[0])) < 1e-13
+    assert norm_rel_err(ctx.apply(x, 0.0, OP_D, PREC_F32)[0], op2.D(x[0])) < 1e-6
+    # a new m0 keeps the loaded term and adds the new mass
+    ctx.set_params(m0=0.3, csw=c["csw"], bc=c["bc"], agg=c["agg"], sap_block=c["sap"], n_tv=4)
+    op3 = dirac.WilsonClover(U, 0.3, c["csw"], bc=c["bc"], A=A2)
+    assert norm_rel_err(ctx.apply(x, 0.2, OP_Q, PREC_F64)[0], op3.Q_sigma(x[0], 0.2)) < 1e-13
+    # NULL: the term built from the gauge field again
+    ctx.load_clover(None)
+    op4 = dirac.WilsonClover(U, 0.3, c["csw"], bc=c["bc"])
+    assert norm_rel_err(ctx.apply(x, 0.2, OP_Q, PREC_F64)[0], op4.Q_sigma(x[0], 0.2)) < 1e-13
+    ctx.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 12])
+def test_stencil_many_right_hand_sides(case, nrhs):
+    """mgeig_apply_dev_nrhs: nrhs fields back to back in one launch, each equal
+    to the oracle's stencil on that field (FP64 1e-13, FP32 1e-6)."""
+    from paper_1509_06865_gb300 import OP_D, OP_Q, PREC_F32, PREC_F64
+    ctx, op, c = case
+    V = ctx.V
+    x = synth.gaussian_vectors(c["dims"], nrhs, 50 + nrhs)
+    ops = ((OP_Q, 0.021), (OP_D, -0.3))
+    wants = {o: [op.Q_sigma(x[k], s) if o == OP_Q else op.D_sigma(x[k], s) for k in range(nrhs)] for o, s in ops}
+    for prec, per, tol in ((PREC_F64, V * 12 * 16, 1e-13), (PREC_F32, V * 12 * 8, 1e-6)):
+        px = ctx.alloc_dev(per * nrhs)
+        py = ctx.alloc_dev(per * nrhs)
+        ctx.pack_spinors(x, px, prec)
+        for opcode, sigma in ops:
+            ctx.apply_dev_nrhs(px, py, nrhs, sigma, opcode, prec)
+            got = ctx.unpack_spinors(py, nrhs, prec)
+            for k in range(nrhs):
+                assert norm_rel_err(got[k], wants[opcode][k]) < tol, (prec, opcode, k)

@@ -69,11 +69,14 @@ def test_free_field_p0_modes_twelvefold():
 
 
 def test_random_field_against_dense_eigh():
-    dims = (4, 4, 4, 4)
-    op = dirac.WilsonClover(synth.gauge_field(dims, 0.3, 1001), -0.4, 1.0)
-    start = synth.gaussian_vectors(dims, 16, 5)
+    from tests import dense4
+    dims = dense4.DENSE4["dims"]
+    op = dense4.field()[1]
+    start = synth.gaussian_vectors(dims, 14, 5)
     lam, V, res, info = chefsi.lowest_abs_eigenpairs(op.Q, start, 8, chefsi.q_norm_bound(op), degree=60)
-    w, v = dense.lowest_eigenpairs(dense.operator_matrix(op.Q, dims), 8)
+    w_all, v_all = dense4.q_eigh()
+    order = np.lexsort((w_all, np.abs(w_all)))[:8]
+    w, v = w_all[order], v_all[:, order]
     assert info["converged"]
     assert np.abs(lam - w).max() <= 1e-12 * np.abs(w).max()
     for i in range(8):
@@ -81,7 +84,5 @@ def test_random_field_against_dense_eigh():
 
 
 def test_norm_bound_holds():
-    dims = (4, 4, 4, 4)
-    op = dirac.WilsonClover(synth.gauge_field(dims, 0.3, 1001), -0.4, 1.0)
-    Qm = dense.operator_matrix(op.Q, dims)
-    assert np.abs(np.linalg.eigvalsh(Qm)).max() <= chefsi.q_norm_bound(op)
+    from tests import dense4
+    assert np.abs(dense4.q_eigh()[0]).max() <= chefsi.q_norm_bound(dense4.field()[1])

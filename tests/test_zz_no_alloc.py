@@ -31,6 +31,14 @@ def make_ctx(precision, dims=DIMS, agg=(4, 4, 4, 4), setup_iters=2):
     return ctx
 
 
+def free_device_bytes():
+    import torch
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info(0)[0]
+
+
+# the FP64 case runs first, in a context of its own, so that the first call
+# after mgeig_create is the one checked
 @pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-4)], ids=["fp64", "mixed"])
 def test_noalloc_cycle_matches_mg_cycle_twice(prec, tol):
     from paper_1509_06865_gb300 import PREC_F32, PREC_F64
@@ -40,14 +48,35 @@ def test_noalloc_cycle_matches_mg_cycle_twice(prec, tol):
     nbytes = V * 12 * (8 if level == PREC_F32 else 16)
     r_dev, z_dev = ctx.alloc_dev(nbytes), ctx.alloc_dev(nbytes)
     rs = synth.gaussian_vectors(DIMS, 2, 11)
-    for call, (r, sigma) in enumerate(((rs[0], 0.03), (rs[1], 0.03))):
-        want = ctx.mg_cycle(r, sigma)
+    # the references first: mgeig_mg_cycle allocates its own transfer buffers
+    wants = [ctx.mg_cycle(r, 0.03) for r in rs]
+    for call, r in enumerate(rs):
         ctx.pack_spinors(r, r_dev, level)
         ctx.pack_spinors(np.zeros_like(r), z_dev, level)
-        ctx.mg_cycle_dev_noalloc(r_dev, z_dev, sigma)
+        free0 = free_device_bytes()
+        ctx.mg_cycle_dev_noalloc(r_dev, z_dev, 0.03)
+        free1 = free_device_bytes()
+        # no device memory is taken by the call (the second call in particular,
+        # after the driver has loaded every kernel it uses)
+        if call == 1:
+            assert free1 == free0, (free0, free1)
         got = ctx.unpack_spinors(z_dev, 1, level)[0]
-        err = norm_rel_err(got, want)
+        err = norm_rel_err(got, wants[call])
         assert err < tol, (call, err)
+    ctx.close()
+
+
+def test_noalloc_rejects_overlapping_r_and_z():
+    from paper_1509_06865_gb300 import MIXED, PREC_F32
+    from paper_1509_06865_gb300._lib import EINVAL, MgeigError
+    ctx = make_ctx(MIXED, setup_iters=0)
+    nbytes = int(np.prod(DIMS)) * 12 * 8
+    buf = ctx.alloc_dev(2 * nbytes)
+    ctx.pack_spinors(synth.gaussian_vectors(DIMS, 1, 3)[0], buf, PREC_F32)
+    for z in (buf, buf + nbytes // 2):
+        with pytest.raises(MgeigError) as e:
+            ctx.mg_cycle_dev_noalloc(buf, z, 0.0)
+        assert e.value.code == EINVAL
     ctx.close()
 
 
