@@ -559,6 +559,41 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# the cost of Algorithm 1 against the number of wanted pairs, and with P built
+# from a subset of the modes (the trend of Fig. 2 and the remark after it, Sec. 2.2)
+
+
+def neig_study(device=0):
+    import torch
+
+    import synth
+    from paper_1509_06865_gb300 import MIXED, Context
+
+    w = WORKLOAD
+    dims = tuple(w["dims"])
+    U = synth.gauge_field(dims, w["eps"], w["seed"])
+    rows = []
+    cases = [(n, -1) for n in (4, 8, 12, 16, 20, 24, 32)] + [(20, 12), (20, 6)]
+    for n_eig, p_modes in cases:
+        ctx = Context(dims, device=device)
+        ctx.set_params(m0=load_m0(), csw=w["csw"], n_tv=20, precision=MIXED, p_modes=p_modes)
+        ctx.load_gauge(U)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.setup(w["seed"])
+        lam, _, res, st = ctx.eigensolve(n_eig, w["tol"], want_vectors=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.close()
+        rows.append(dict(n_eig=n_eig, p_modes=p_modes if p_modes > 0 else 20, s=e0.elapsed_time(e1) / 1e3,
+                         converged=st["converged"], max_resid=float(res.max()), sweeps=st["sweeps"],
+                         solves=st["solves"], outer_iters=st["outer_iters"], coarse_iters=st["coarse_iters"]))
+        print(json.dumps(rows[-1]), flush=True)
+    return rows
+
+
+# ---------------------------------------------------------------------------
 # small self-terminating cases for ncu (one GPU, a few GB)
 
 
@@ -611,6 +646,8 @@ def main():
     ap.add_argument("--no-north-star", action="store_true", help="skip the 32^3x64 eigensolve")
     ap.add_argument("--north-star-fp64", action="store_true", help="also the all-FP64 32^3x64 eigensolve")
     ap.add_argument("--profile-case", choices=["eig16", "stencil32"])
+    ap.add_argument("--neig-study", action="store_true",
+                    help="time Algorithm 1 on the 16^3x32 field for 4..32 wanted pairs and with P from 12 / 6 modes")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
@@ -618,6 +655,9 @@ def main():
         return
     if args.profile_case:
         profile_case(args.profile_case)
+        return
+    if args.neig_study:
+        neig_study()
         return
     if args.impl == "reference":
         run_reference(args)

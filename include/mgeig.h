@@ -142,6 +142,10 @@ typedef struct mgeig_params {
     int coarse_links;     /* MGEIG_LINKS_*: how the coarse operator is stored and
                              read by the coarse solver and coarse applies (16-bit
                              links only with MGEIG_MIXED)                        */
+    int p_modes;          /* P is built from the first p_modes iterated vectors of
+                             Algorithm 1 and the setup's test vectors p_modes ..
+                             n_tv - 1 (kept as the setup left them); -1 = n_tv:
+                             every test vector is replaced by a mode            */
     double barrier_timeout;   /* seconds (of SM clock) a block of the persistent
                              coarse solver waits at a grid barrier before it gives
                              up, raises MGEIG_ETIMEOUT and returns              */
@@ -327,6 +331,26 @@ int mgeig_mg_cycle_dev_noalloc(mgeig_ctx *ctx, double sigma, const void *r, void
 int mgeig_solve(mgeig_ctx *ctx, double sigma, const double *b, double *x, double tol,
                 mgeig_stats *stats);
 
+/* Many shifted systems of many fields (Algorithm 1's shifted systems, and the
+ * Z2 noise right-hand sides of Sec. 3, Eqs. 3.4-3.6): for every context k
+ * (set up, any lattice, any device) solve (Q - sigmas[s]) x = b_j for the nsig
+ * shifts and the nrhs host right-hand sides b[k] (nrhs spinors of that lattice
+ * one after another) to relative residual tol with the FGMRES of mgeig_solve;
+ * x[k] receives nsig * nrhs solutions ordered [shift][rhs].  The systems of a
+ * context run one after another, shift-major (the coarse deflation data of a
+ * shift is computed once for all its right-hand sides).  Returns ENOCONV when
+ * any system hits outer_maxiter (all outputs filled), the first other error of a
+ * context otherwise.  stats (may be NULL) sums the counters of all contexts. */
+int mgeig_solve_batch(mgeig_ctx *const *ctxs, int nctx, const double *sigmas, int nsig, const double *const *b,
+                      double *const *x, int nrhs, double tol, mgeig_stats *stats);
+
+/* Solve the non-Hermitian (D - sigma gamma5) x = b (sigma = 0: the Wilson-clover
+ * system D x = b that DD-alpha-AMG solves, Sec. 2) with the same FP64 flexible
+ * GMRES, now on D_sigma, right-preconditioned by B gamma5 (D_sigma^-1 =
+ * (Q - sigma)^-1 gamma5; with the SAP smoother this is the two-grid method on
+ * D_sigma itself, SAP acting on D_sigma z = r).  ENOCONV if outer_maxiter is hit. */
+int mgeig_solve_d(mgeig_ctx *ctx, double sigma, const double *b, double *x, double tol, mgeig_stats *stats);
+
 /* Algorithm 1: the n_eig eigenpairs of Q of smallest |lambda| to eigen-residual
  * ||Q v - lambda v|| <= tol, starting from the setup's test vectors (rotated to
  * Ritz vectors of Q in their span, ordered by |theta|).  The iteration runs on
@@ -367,6 +391,39 @@ int mgeig_get_stream(mgeig_ctx *ctx, void **stream);
  * calls, including mgeig_load_gauge*); *count is written on success.  The
  * paper has no counterpart: it lets a caller count the device work of a step. */
 int mgeig_get_launch_count(mgeig_ctx *ctx, long long *count);
+
+/* ---------------------------------------------------------------------------
+ * Approximate low-mode averaging (Sec. 3.1, 3.2): eigenpairs of low accuracy,
+ * e.g. the setup's test vectors (Sec. 3.3: no Rayleigh quotient iteration),
+ * used through the corrected low-mode inverse and an oblique projector.
+ * -------------------------------------------------------------------------- */
+
+/* Take n approximate eigenvectors (host spinors V, or NULL for the Ritz vectors of
+ * Q in the span of the setup's first n test vectors, by |theta|), orthonormalise
+ * them (Gram-Schmidt in FP64) and keep the
+ * pairs whose relative accuracy passes the cutoff eps_i / |lambda_i| <= cutoff
+ * (Sec. 3.3 uses 0.75), lambda_i = <v_i|Q|v_i>, eps_i = ||Q v_i - lambda_i v_i||.
+ * Outputs (any may be NULL): lam[n], eps[n], kept[n] (1 kept, 0 cut), *n_kept;
+ * A[k][k] and Ainv[k][k] (complex128, row-major, k = *n_kept) with
+ * A_ij = <v_i|Q|v_j> over the kept pairs in their original order; Llow[Lt]
+ * (complex128) the low-mode part of the loop per timeslice,
+ * L_low(t) = sum_{x in t} tr (Q~^-1_low)_{x,x},  Q~^-1_low = sum_ij (A^-1)_ij |v_i><v_j|.
+ * The state stays in the context for mgeig_lma_apply / mgeig_lma_loop_high. */
+int mgeig_lma_prepare(mgeig_ctx *ctx, int n, const double *V, double cutoff, double *lam, double *eps, int *kept,
+                      int *n_kept, double *A, double *Ainv, double *Llow);
+
+/* y = Q~^-1_low x (mode 0) or y = R~ x with the oblique projector
+ * R~ = 1 - sum_ij Q |v_i> (A^-1)_ij <v_j| (mode 1), host spinors, FP64. */
+int mgeig_lma_apply(mgeig_ctx *ctx, int mode, const double *x, double *y);
+
+/* The high-mode part of the loop per timeslice, estimated with nstoch Z2 + iZ2
+ * noise vectors eta_n (Philox key seed, stream 0x5EED0002: the entries
+ * (+-1 +- i)/sqrt 2 from the sign bits of the words of counter (site, component
+ * pair, n, stream)):  Lhigh[t] = 1/nstoch sum_n sum_{x in t} <eta_n(x)|s_n(x)>, where
+ * Q s_n = R~ eta_n is solved by the FGMRES of mgeig_solve (sigma = 0) to relative
+ * residual tol, so that Q^-1 R~ = Q^-1 - Q~^-1_low (Sec. 3.1 with the oblique
+ * projector of Sec. 3.2).  Needs mgeig_lma_prepare and mgeig_setup. */
+int mgeig_lma_loop_high(mgeig_ctx *ctx, int nstoch, uint64_t seed, double tol, double *Lhigh, mgeig_stats *stats);
 
 /* ---------------------------------------------------------------------------
  * The learned smoother (the paper has none; spec extension of the

@@ -35,7 +35,7 @@ class Params(C.Structure):
         ("n_guard", C.c_int), ("coarse_deflate", C.c_int), ("ritz_each_sweep", C.c_int),
         ("shift_floor", C.c_double), ("guard_maxiter", C.c_int), ("ritz_keep", C.c_double),
         ("fine_deflate", C.c_int), ("fine_deflate_radius", C.c_double),
-        ("adaptive_tol", C.c_int), ("ritz_start", C.c_int), ("coarse_links", C.c_int),
+        ("adaptive_tol", C.c_int), ("ritz_start", C.c_int), ("coarse_links", C.c_int), ("p_modes", C.c_int),
         ("barrier_timeout", C.c_double),
     ]
 
@@ -97,6 +97,8 @@ def load():
         "mgeig_sap": (I, [P, D, P, P, I]),
         "mgeig_mg_cycle": (I, [P, D, P, P]),
         "mgeig_solve": (I, [P, D, P, P, D, C.POINTER(Stats)]),
+        "mgeig_solve_d": (I, [P, D, P, P, D, C.POINTER(Stats)]),
+        "mgeig_solve_batch": (I, [P, I, P, I, P, P, I, D, C.POINTER(Stats)]),
         "mgeig_eigensolve": (I, [P, I, D, P, P, P, C.POINTER(Stats)]),
         "mgeig_set_timing": (I, [P, I]),
         "mgeig_set_timing_classes": (I, [P, C.c_uint]),
@@ -105,6 +107,9 @@ def load():
         "mgeig_get_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
         "mgeig_mg_cycle_dev_noalloc": (I, [P, D, P, P]),
         "mgeig_fma_peak": (I, [P, I, I, C.POINTER(D)]),
+        "mgeig_lma_prepare": (I, [P, I, P, D, P, P, P, P, P, P, P]),
+        "mgeig_lma_apply": (I, [P, I, P, P]),
+        "mgeig_lma_loop_high": (I, [P, I, C.c_uint64, D, P, C.POINTER(Stats)]),
         "mgeig_net_init": (I, [P, C.c_uint64]),
         "mgeig_net_set_weights": (I, [P, P]),
         "mgeig_net_get_weights": (I, [P, P]),
@@ -127,6 +132,27 @@ def _ptr(a: np.ndarray):
 
 def _c128(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def solve_batch(ctxs, sigmas, rhs, tol=1e-10):
+    """(Q - sigma_s) x = b_j for every context (rhs[k]: [nrhs, ...] spinors of context k's
+    lattice, the same nrhs for all): list of arrays [nsig, nrhs, ...] and the summed stats."""
+    lib = load()
+    n = len(ctxs)
+    sig = np.ascontiguousarray(sigmas, dtype=np.float64)
+    bs = [_c128(b) for b in rhs]
+    nrhs = bs[0].shape[0]
+    assert all(b.shape[0] == nrhs for b in bs)
+    xs = [np.empty((len(sig),) + b.shape, dtype=np.complex128) for b in bs]
+    hp = (C.c_void_p * n)(*[c._h.value for c in ctxs])
+    bp = (C.c_void_p * n)(*[b.ctypes.data for b in bs])
+    xp = (C.c_void_p * n)(*[x.ctypes.data for x in xs])
+    st = Stats()
+    rc = lib.mgeig_solve_batch(C.cast(hp, C.c_void_p), n, _ptr(sig), len(sig), C.cast(bp, C.c_void_p),
+                               C.cast(xp, C.c_void_p), nrhs, float(tol), C.byref(st))
+    if rc not in (OK, ENOCONV):
+        raise MgeigError("mgeig_solve_batch", rc, lib.mgeig_strerror(rc).decode())
+    return xs, dict(st.as_dict(), converged=rc == OK)
 
 
 class Context:
@@ -327,6 +353,15 @@ class Context:
                                                              C.byref(st)), allow=(ENOCONV,))
         return x, dict(st.as_dict(), converged=rc == OK)
 
+    def solve_d(self, b, sigma=0.0, tol=1e-10):
+        """(D - sigma gamma5) x = b (non-Hermitian), FGMRES with the two-grid preconditioner."""
+        b = _c128(b)
+        x = np.empty_like(b)
+        st = Stats()
+        rc = self._check("mgeig_solve_d", self.lib.mgeig_solve_d(self._h, float(sigma), _ptr(b), _ptr(x),
+                                                                 float(tol), C.byref(st)), allow=(ENOCONV,))
+        return x, dict(st.as_dict(), converged=rc == OK)
+
     def eigensolve(self, n_eig: int, tol: float, want_vectors: bool = True):
         evals = np.empty(n_eig)
         resid = np.empty(n_eig)
@@ -343,6 +378,42 @@ class Context:
         s = C.c_void_p()
         self._check("mgeig_get_stream", self.lib.mgeig_get_stream(self._h, C.byref(s)))
         return s.value or 0
+
+    # ---- approximate low-mode averaging -------------------------------------
+    def lma_prepare(self, n: int, V=None, cutoff: float = 0.75):
+        """Approximate modes V (n host spinors, None: the setup's first n test
+        vectors): dict of lam, eps, kept, A, Ainv (kept x kept), Llow[Lt]."""
+        lam, eps = np.empty(n), np.empty(n)
+        kept = np.empty(n, dtype=np.int32)
+        nk = C.c_int()
+        A = np.empty((n, n), dtype=np.complex128)
+        Ai = np.empty((n, n), dtype=np.complex128)
+        Llow = np.empty(self.dims[3], dtype=np.complex128)
+        Vp = None
+        if V is not None:
+            V = _c128(V)
+            assert V.size == n * self.V * 12
+            Vp = _ptr(V)
+        self._check("mgeig_lma_prepare", self.lib.mgeig_lma_prepare(self._h, int(n), Vp, float(cutoff), _ptr(lam),
+                                                                    _ptr(eps), _ptr(kept), C.byref(nk), _ptr(A),
+                                                                    _ptr(Ai), _ptr(Llow)))
+        k = nk.value
+        return dict(lam=lam, eps=eps, kept=kept.astype(bool), n_kept=k,
+                    A=A.reshape(-1)[:k * k].reshape(k, k).copy(), Ainv=Ai.reshape(-1)[:k * k].reshape(k, k).copy(),
+                    Llow=Llow)
+
+    def lma_apply(self, x, mode: int):
+        x = _c128(x)
+        y = np.empty_like(x)
+        self._check("mgeig_lma_apply", self.lib.mgeig_lma_apply(self._h, int(mode), _ptr(x), _ptr(y)))
+        return y
+
+    def lma_loop_high(self, nstoch: int, seed: int, tol: float = 1e-10):
+        L = np.empty(self.dims[3], dtype=np.complex128)
+        st = Stats()
+        self._check("mgeig_lma_loop_high", self.lib.mgeig_lma_loop_high(self._h, int(nstoch), C.c_uint64(seed),
+                                                                        float(tol), _ptr(L), C.byref(st)))
+        return L, st.as_dict()
 
     # ---- learned smoother ------------------------------------------------
     def net_init(self, seed: int):

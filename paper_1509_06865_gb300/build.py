@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgeig.so")
-SOURCES = ["fine_op.cu", "blas.cu", "mg.cu", "coarse_gmres.cu", "solver.cu", "abi.cu", "peak.cu", "links16.cu", "learned.cu"]
+SOURCES = ["fine_op.cu", "blas.cu", "mg.cu", "coarse_gmres.cu", "solver.cu", "abi.cu", "peak.cu", "links16.cu", "learned.cu", "lma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -59,6 +59,7 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (p.coarse_links < MGEIG_LINKS_LEVEL || p.coarse_links > MGEIG_LINKS_F16) return MGEIG_EINVAL;
     if (p.coarse_links != MGEIG_LINKS_LEVEL && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (!(p.barrier_timeout > 0) || !(p.barrier_timeout <= 60)) return MGEIG_EINVAL;
+    if (p.p_modes < -1 || p.p_modes == 0) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES && p.smoother != MGEIG_LEARNED) return MGEIG_EINVAL;
@@ -126,6 +127,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->ritz_start = 1;
     p->coarse_links = MGEIG_LINKS_LEVEL;
     p->barrier_timeout = 2.0;
+    p->p_modes = -1;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
@@ -179,6 +181,7 @@ void mgeig_destroy(mgeig_ctx *ctx) {
     try { c.timer.reset(); } catch (...) {}
     mg_free(c);
     net_free(c);
+    lma_free(c);
     c.U64.free(); c.U32.free(); c.clov64.free(); c.clov32.free(); c.clov_user.free(); c.staging.free();
     c.red_partial.free(); c.red_out.free(); c.Dc.free(); c.Dc16.free(); c.Dcs.free();
     for (auto &b : c.user_bufs) b.free();
@@ -422,6 +425,7 @@ int mgeig_set_test_vectors(mgeig_ctx *ctx, const double *W) {
         int rc = need_setup(c);
         if (rc) return rc;
         for (int j = 0; j < c.prm.n_tv; ++j) host_to_internal(c, W + (size_t)j * c.fine_ncpx() * 2, mg_test_vector(c, j));
+        mg_use_test_vectors(c);
         mg_rebuild(c);
         sync(c);
         c.have_setup = true;
@@ -611,6 +615,69 @@ int mgeig_solve(mgeig_ctx *ctx, double sigma, const double *b, double *x, double
     });
 }
 
+int mgeig_solve_batch(mgeig_ctx *const *ctxs, int nctx, const double *sigmas, int nsig, const double *const *b,
+                      double *const *x, int nrhs, double tol, mgeig_stats *stats) {
+    if (!ctxs || nctx < 1 || !sigmas || nsig < 1 || !b || !x || nrhs < 1 || !(tol > 0)) return MGEIG_EINVAL;
+    for (int k = 0; k < nctx; ++k)
+        if (!ctxs[k] || !b[k] || !x[k]) return MGEIG_EINVAL;
+    for (int s = 0; s < nsig; ++s)
+        if (!std::isfinite(sigmas[s])) return MGEIG_EINVAL;
+    mgeig_stats total{};
+    int status = MGEIG_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int k = 0; k < nctx; ++k) {
+        int rc = guarded(ctxs[k], [&](Ctx &c) {
+            if (!c.have_setup) return MGEIG_ENOTSETUP;
+            begin_stats(c);
+            const size_t nd = c.fine_ncpx() * 2;   // doubles per host spinor
+            TmpBuf a, bb;
+            a.alloc(spinor_bytes(c));
+            bb.alloc(spinor_bytes(c));
+            int worst = MGEIG_OK;
+            // shift-major order: the coarse deflation data of a shift serves all right-hand sides
+            for (int s = 0; s < nsig; ++s)
+                for (int r = 0; r < nrhs; ++r) {
+                    host_to_internal(c, b[k] + nd * r, a.p);
+                    const int rc1 = fgmres_solve(c, sigmas[s], a.p, bb.p, tol);
+                    if (rc1 != MGEIG_OK && rc1 != MGEIG_ENOCONV) return rc1;
+                    if (rc1 == MGEIG_ENOCONV) worst = MGEIG_ENOCONV;
+                    internal_to_host(c, bb.p, x[k] + nd * ((size_t)s * nrhs + r));
+                }
+            coarse_iters_take(c);
+            c.st.kernel_launches += c.launches;
+            total.solves += c.st.solves;
+            total.outer_iters += c.st.outer_iters;
+            total.mg_cycles += c.st.mg_cycles;
+            total.coarse_iters += c.st.coarse_iters;
+            total.fine_applies += c.st.fine_applies;
+            total.kernel_launches += c.st.kernel_launches;
+            return worst;
+        });
+        if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
+        if (rc == MGEIG_ENOCONV) status = MGEIG_ENOCONV;
+    }
+    total.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = total;
+    return status;
+}
+
+int mgeig_solve_d(mgeig_ctx *ctx, double sigma, const double *b, double *x, double tol, mgeig_stats *stats) {
+    if (!b || !x || !(tol > 0)) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_setup) return MGEIG_ENOTSETUP;
+        auto t0 = std::chrono::steady_clock::now();
+        begin_stats(c);
+        TmpBuf a, bb;
+        a.alloc(spinor_bytes(c));
+        bb.alloc(spinor_bytes(c));
+        host_to_internal(c, b, a.p);
+        int rc = fgmres_solve_d(c, sigma, a.p, bb.p, tol);
+        internal_to_host(c, bb.p, x);
+        end_stats(c, stats, t0);
+        return rc;
+    });
+}
+
 int mgeig_eigensolve(mgeig_ctx *ctx, int n_eig, double tol, double *evals, double *evecs, double *resid,
                      mgeig_stats *stats) {
     return guarded(ctx, [&](Ctx &c) {
@@ -657,6 +724,52 @@ int mgeig_kernel_times(mgeig_ctx *ctx, int n, long long *launches, double *ms, d
             if (names) names[k] = kNames[k];
         }
         return (int)K_NCLASS;
+    });
+}
+
+int mgeig_lma_prepare(mgeig_ctx *ctx, int n, const double *V, double cutoff, double *lam, double *eps, int *kept,
+                      int *n_kept, double *A, double *Ainv, double *Llow) {
+    if (n < 1 || n > MAX_ITERATED || !(cutoff > 0)) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.have_gauge) return MGEIG_ENOTSETUP;
+        if (!V && !c.have_setup) return MGEIG_ENOTSETUP;
+        if (!V && n > c.prm.n_tv) return MGEIG_EINVAL;
+        void *dev = lma_vectors(c, n);
+        const size_t sb = spinor_bytes(c);
+        for (int i = 0; i < n; ++i) {
+            void *dst = static_cast<char *>(dev) + sb * i;
+            if (V) host_to_internal(c, V + (size_t)i * c.fine_ncpx() * 2, dst);
+            else MG_CUDA(cudaMemcpyAsync(dst, mg_test_vector(c, i), sb, cudaMemcpyDeviceToDevice, c.stream));
+        }
+        lma_prepare(c, n, dev, V == nullptr, cutoff, lam, eps, kept, n_kept, A, Ainv, Llow);
+        sync(c);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_lma_apply(mgeig_ctx *ctx, int mode, const double *x, double *y) {
+    if (!x || !y || (mode != 0 && mode != 1)) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.lma) return MGEIG_ENOTSETUP;
+        TmpBuf a, b;
+        a.alloc(spinor_bytes(c));
+        b.alloc(spinor_bytes(c));
+        host_to_internal(c, x, a.p);
+        lma_apply(c, mode, a.p, b.p);
+        internal_to_host(c, b.p, y);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_lma_loop_high(mgeig_ctx *ctx, int nstoch, uint64_t seed, double tol, double *Lhigh, mgeig_stats *stats) {
+    if (nstoch < 1 || !(tol > 0) || !Lhigh) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        if (!c.lma || !c.have_setup) return MGEIG_ENOTSETUP;
+        auto t0 = std::chrono::steady_clock::now();
+        begin_stats(c);
+        lma_loop_high(c, nstoch, seed, tol, Lhigh, nullptr);
+        end_stats(c, stats, t0);
+        return MGEIG_OK;
     });
 }
 

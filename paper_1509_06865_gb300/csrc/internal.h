@@ -98,6 +98,7 @@ struct TimeScope {
 
 struct Ctx;
 struct Net;   // the learned smoother's weights and activations (learned.cu)
+struct Lma;   // approximate low-mode averaging state (solver.cu)
 
 // ----- fine operator (fine_op.cu) -----
 void pack_gauge(Ctx &c, const double *dev_host_layout);
@@ -219,6 +220,7 @@ struct Ctx {
     struct Work;
     Work *work = nullptr;
     Net *net = nullptr;       // the learned smoother (allocated on first use)
+    Lma *lma = nullptr;       // approximate low-mode averaging (mgeig_lma_prepare)
 };
 
 // ----- solvers (solver.cu) -----
@@ -231,6 +233,7 @@ void mg_alloc(Ctx &c);
 void coarse_iters_take(Ctx &c);
 void mg_free(Ctx &c);
 void *mg_test_vector(Ctx &c, int j);
+void mg_use_test_vectors(Ctx &c);   // P is rebuilt from the test vectors (not the eigensolver's modes)
 void mg_rebuild(Ctx &c);   // P and coarse operator from c.W
 void setup(Ctx &c, uint64_t seed);
 void mg_cycle_host(Ctx &c, double sigma, const double *r_dev64_internal, double *z_dev64_internal);
@@ -239,6 +242,7 @@ int mg_cycle_noalloc(Ctx &c, double sigma, const void *r, void *z);
 size_t mg_cycle_noalloc_limit();
 void noalloc_prepare(Ctx &c);   // the static array's address, looked up once per device
 int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol, int maxiter = 0);
+int fgmres_solve_d(Ctx &c, double sigma, const void *b64, void *x64, double tol);
 int eigensolve(Ctx &c, int n_eig, double tol, double *evals, double *evecs_host, double *resid);
 void sap_smooth_f64(Ctx &c, double sigma, const void *b64, void *z64, int cycles);
 void coarse_apply_f64(Ctx &c, double sigma, const void *x64, void *y64);
@@ -261,6 +265,18 @@ void net_smooth(Ctx &c, const void *r, void *z);
 double net_train_step(Ctx &c, const void *r, const void *e, int batch, double lr);
 // loss and weight gradients for host channel data x, t [batch][V][24] FP64
 double net_loss_grads(Ctx &c, const double *x, const double *t, int batch, float *G_host);
+// ----- approximate low-mode averaging (lma.cu kernels, solver.cu host code) -----
+// M[t][j][i] = sum_{x in timeslice t} <X_j(x) | Y_i(x)> for FP64 internal spinors (device output)
+void timeslice_dots(Ctx &c, const void *const *X, int nj, const void *const *Y, int ni, void *M_dev);
+void z2_spinors(Ctx &c, uint64_t seed, void *out64, int n, uint32_t tag);
+// n FP64 internal vectors at V (device, overwritten by their orthonormalisation);
+// outputs as in mgeig_lma_prepare (any may be NULL)
+void lma_prepare(Ctx &c, int n, void *V, bool ritz, double cutoff, double *lam, double *eps, int *kept, int *n_kept,
+                 double *A, double *Ainv, double *Llow);
+void *lma_vectors(Ctx &c, int n);   // device room for n FP64 spinors owned by the LMA state
+void lma_apply(Ctx &c, int mode, const void *x64, void *y64);
+void lma_loop_high(Ctx &c, int nstoch, uint64_t seed, double tol, double *Lhigh, int *outer_iters);
+void lma_free(Ctx &c);
 // training pairs from the method and the training loop (solver.cu)
 void net_train(Ctx &c, int steps, int batch, double lr, uint64_t seed, double *losses);
 // FMA throughput (FLOP/s) of the library's own peak kernel, FP64 or FP32 (peak.cu)

@@ -14,6 +14,7 @@
 #include <numeric>
 
 #include <cstdlib>
+#include <cstring>
 
 #include <mutex>
 
@@ -162,6 +163,7 @@ struct Ctx::Work {
     DevBuf cgS;                  // persistent coarse solver's global scratch
     DevBuf Wc, AWc, Edev, Einv;  // deflation: P^dag w_j, (Q_c - sigma) P^dag w_j, E, E^-1
     DevBuf Mextra, Xall;         // Algorithm 1 vectors beyond the N_tv test vectors; rotation scratch
+    DevBuf Wfrozen;              // the setup's test vectors that stay in P (p_modes < N_tv)
     std::vector<void *> modes;   // iterated vectors: W[0..N_tv) then the extra ones
     std::vector<void *> Psrc;    // the N_tv vectors P is built from (W, or the first iterated vectors)
     bool defl_valid = false;
@@ -177,6 +179,7 @@ struct Ctx::Work {
     std::vector<cpx<double>> Gz, Hz;       // Z^dag Z and Z^dag Q Z (row-major, fd_n x fd_n)
     int fd_n = 0;                          // maintained vectors (0: deflation off)
     int fd_k = 0;                          // vectors of the active deflation (0: off)
+    int fg_mode = MODE_QSIGMA;             // operator of the FGMRES: Q - sigma, or D - sigma gamma5
 };
 
 static size_t f64_bytes(const Ctx &c) { return c.fine_ncpx() * sizeof(double2); }
@@ -247,7 +250,7 @@ void mg_free(Ctx &c) {
     w.rc.free(); w.ec.free(); w.ct.free();
     w.cgS.free();
     w.Wc.free(); w.AWc.free(); w.Edev.free(); w.Einv.free();
-    w.Mextra.free(); w.Xall.free();
+    w.Mextra.free(); w.Xall.free(); w.Wfrozen.free();
     w.QZ64all.free(); w.ZRall.free(); w.QZRall.free(); w.AZRall.free(); w.fdEinv.free(); w.fdCoef.free();
     delete c.work;
     c.work = nullptr;
@@ -256,6 +259,7 @@ void mg_free(Ctx &c) {
 }
 
 void *mg_test_vector(Ctx &c, int j) { return c.work->W[j]; }
+void mg_use_test_vectors(Ctx &c) { c.work->Psrc = c.work->W; }
 
 // ---------------------------------------------------------------------------
 // Givens-based least squares of GMRES (host)
@@ -792,9 +796,13 @@ static void precondition(Ctx &c, double sigma, const void *v64, void *z) {
     Ctx::Work &w = *c.work;
     const size_t n = c.fine_ncpx();
     const int k = w.fd_k;
+    const bool dsys = w.fg_mode == MODE_DSIGMA;
     if (sizeof(R) == 4) convert_f64_to_f32(c, v64, w.rR.p, n);
-    else if (k) blas_copy<double>(c, v64, w.rR.p, n);
-    const void *r = (sizeof(R) == 4 || k) ? w.rR.p : v64;
+    else if (k || dsys) blas_copy<double>(c, v64, w.rR.p, n);
+    // for D - sigma gamma5 = gamma5 (Q - sigma) the preconditioner is B gamma5
+    // (the lower spins are the second half of either layout: FP64 [12][V], FP32 float4 [6][V])
+    if (dsys) blas_scale<R>(c, cpx<double>(-1), static_cast<char *>(w.rR.p) + n / 2 * sizeof(cpx<R>), n / 2);
+    const void *r = (sizeof(R) == 4 || k || dsys) ? w.rR.p : v64;
     cpx<double> *cf = w.fdCoef.as<cpx<double>>();
     cpx<double> *d = cf + MAX_ITERATED, *unused = cf + 2 * MAX_ITERATED;
     if (k) {
@@ -827,7 +835,7 @@ static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol,
     Hess H(m);
     while (its < maxiter) {
         if (have_x) {
-            apply_fine<double>(c, MODE_QSIGMA, sigma, x, V[0]);
+            apply_fine<double>(c, w.fg_mode, sigma, x, V[0]);
             blas_scale<double>(c, cpx<double>(-1), V[0], n);
             blas_axpy<double>(c, cpx<double>(1), b, V[0], n);
         } else {
@@ -846,8 +854,8 @@ static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol,
         for (int j = 0; j < mm; ++j) {
             void *zj = w.Z[j].p;
             precondition<R>(c, sigma, V[j], zj);
-            if (sizeof(R) == 4) apply_fine_f64_from_f32(c, MODE_QSIGMA, sigma, zj, V[j + 1]);
-            else apply_fine<double>(c, MODE_QSIGMA, sigma, zj, V[j + 1]);
+            if (sizeof(R) == 4) apply_fine_f64_from_f32(c, w.fg_mode, sigma, zj, V[j + 1]);
+            else apply_fine<double>(c, w.fg_mode, sigma, zj, V[j + 1]);
             const double nrm = arnoldi_step<double>(c, V, j, V[j + 1], n, H);
             est = H.add_column(j);
             k = j + 1;
@@ -862,6 +870,15 @@ static int fgmres_impl(Ctx &c, double sigma, const void *b, void *x, double tol,
         if (est <= tol * bnorm) return MGEIG_OK;
     }
     return MGEIG_ENOCONV;
+}
+
+// (D - sigma gamma5) x = b, the non-Hermitian system of DD-alpha-AMG (Sec. 2),
+// by the same FGMRES with the preconditioner B gamma5 (D_sigma^-1 = (Q - sigma)^-1 gamma5)
+int fgmres_solve_d(Ctx &c, double sigma, const void *b64, void *x64, double tol) {
+    Ctx::Work &w = *c.work;
+    w.fg_mode = MODE_DSIGMA;
+    struct Reset { Ctx::Work &w; ~Reset() { w.fg_mode = MODE_QSIGMA; } } reset{w};
+    return fgmres_solve(c, sigma, b64, x64, tol);
 }
 
 int fgmres_solve(Ctx &c, double sigma, const void *b64, void *x64, double tol, int maxiter) {
@@ -1006,7 +1023,22 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
     }
     std::vector<void *> &M = w.modes;
     if (c.prm.ritz_start) ritz_rotate(c, M, std::max(ntv, n_eig));
-    w.Psrc.assign(M.begin(), M.begin() + ntv);
+    // P from the first p iterated vectors and, when p < N_tv, the setup's test
+    // vectors p .. N_tv - 1 (a frozen copy): a P built from a subset of the modes
+    const int p_modes = c.prm.p_modes < 0 ? ntv : std::min(c.prm.p_modes, ntv);
+    std::vector<void *> Wfix;
+    if (p_modes < ntv) {
+        w.Wfrozen.alloc(f64_bytes(c) * (ntv - p_modes));
+        for (int j = p_modes; j < ntv; ++j) {
+            Wfix.push_back(w.Wfrozen.as<char>() + f64_bytes(c) * (j - p_modes));
+            blas_copy<double>(c, M[j], Wfix.back(), N);
+        }
+    }
+    auto set_psrc = [&]() {
+        w.Psrc.assign(M.begin(), M.begin() + p_modes);
+        w.Psrc.insert(w.Psrc.end(), Wfix.begin(), Wfix.end());
+    };
+    set_psrc();
     mg_rebuild(c);
     std::vector<double> lam(n_eig, 0.0), eps(n_eig, 1.0);
     fdefl_begin(c, M, n_eig);
@@ -1055,7 +1087,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             MG_REQUIRE(std::isfinite(nrm) && nrm > 0, MGEIG_EBREAKDOWN);
             blas_scale<double>(c, cpx<double>(1.0 / nrm), w.x64.p, N);
             blas_copy<double>(c, w.x64.p, M[i], N);
-            if (i < ntv) mg_rebuild(c);   // P holds the first N_tv iterated vectors
+            if (i < p_modes) mg_rebuild(c);   // P holds the first p_modes iterated vectors
             w.fd_k = 0;   // the solve is over
             if (w.fd_n) fdefl_update(c, M, i);
             auto le = rayleigh(c, M[i]);
@@ -1105,7 +1137,7 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
             std::vector<double> l2(n_eig), e2(n_eig);
             for (int k = 0; k < n_eig; ++k) { M2[k] = M[perm[k]]; l2[k] = lam[perm[k]]; e2[k] = eps[perm[k]]; }
             for (int k = 0; k < n_eig; ++k) { M[k] = M2[k]; lam[k] = l2[k]; eps[k] = e2[k]; }
-            w.Psrc.assign(M.begin(), M.begin() + ntv);
+            set_psrc();
             mg_rebuild(c);
             fdefl_all(c, M);
             if (log_on()) {
@@ -1151,6 +1183,144 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
         }
     }
     return status;
+}
+
+// ---------------------------------------------------------------------------
+// Approximate low-mode averaging (Sec. 3.1, 3.2): from N orthonormal approximate
+// eigenvectors v_i, the pairs that pass the cutoff eps_i / |lambda_i| <= c,
+// A_ij = <v_i | Q | v_j>, Q~^-1_low = sum (A^-1)_ij |v_i><v_j|, the oblique
+// projector R~ = 1 - sum Q |v_i> (A^-1)_ij <v_j|, and the two parts of the loop
+// L(t) = sum_{x in t} tr Q^-1_{x,x}: the low-mode part from the vectors, the
+// high-mode part Q^-1 R~ stochastically with Z2 noise (Q s = R~ eta).
+
+struct Lma {
+    DevBuf Vall, QVall;                 // N vectors and Q v_i (FP64)
+    int n = 0;
+    std::vector<void *> V, QV;          // the kept vectors and their products
+    std::vector<cpx<double>> Ainv;      // row-major, kept x kept
+};
+
+void *lma_vectors(Ctx &c, int n) {
+    if (!c.lma) c.lma = new Lma();
+    c.lma->Vall.alloc(f64_bytes(c) * n);
+    c.lma->QVall.alloc(f64_bytes(c) * n);
+    return c.lma->Vall.p;
+}
+
+void lma_free(Ctx &c) {
+    if (!c.lma) return;
+    c.lma->Vall.free();
+    c.lma->QVall.free();
+    delete c.lma;
+    c.lma = nullptr;
+}
+
+void lma_prepare(Ctx &c, int n, void *Vdev, bool ritz, double cutoff, double *lam, double *eps, int *kept,
+                 int *n_kept, double *A_out, double *Ainv_out, double *Llow) {
+    Lma &L = *c.lma;
+    MG_REQUIRE(Vdev == L.Vall.p && n >= 1 && n <= MAX_ITERATED, MGEIG_EINVAL);
+    const size_t N = c.fine_ncpx();
+    std::vector<void *> V(n), QV(n);
+    for (int i = 0; i < n; ++i) {
+        V[i] = L.Vall.as<char>() + f64_bytes(c) * i;
+        QV[i] = L.QVall.as<char>() + f64_bytes(c) * i;
+    }
+    orthonormalise(c, V, n);
+    if (ritz) ritz_rotate(c, V, n);   // Ritz vectors of Q in span(V), by |theta|
+    L.V.clear();
+    L.QV.clear();
+    for (int i = 0; i < n; ++i) {
+        auto le = rayleigh(c, V[i]);
+        apply_fine<double>(c, MODE_QSIGMA, 0.0, V[i], QV[i]);
+        if (lam) lam[i] = le.first;
+        if (eps) eps[i] = le.second;
+        const bool keep = le.second <= cutoff * std::fabs(le.first);
+        if (kept) kept[i] = keep ? 1 : 0;
+        if (keep) { L.V.push_back(V[i]); L.QV.push_back(QV[i]); }
+    }
+    const int nk = (int)L.V.size();
+    L.n = nk;
+    if (n_kept) *n_kept = nk;
+    L.Ainv.clear();
+    if (!nk) return;
+    std::vector<cpx<double>> A((size_t)nk * nk);
+    std::vector<const void *> X(L.V.begin(), L.V.end());
+    for (int j = 0; j < nk; ++j) {
+        blas_multidot<double>(c, X.data(), nk, L.QV[j], N, dslot(c, H1));
+        fetch(c, H1 + nk);
+        for (int i = 0; i < nk; ++i) A[(size_t)i * nk + j] = *hslot(c, H1 + i);   // <v_i | Q v_j>
+    }
+    MG_REQUIRE(invert(nk, A, L.Ainv), MGEIG_EBREAKDOWN);
+    if (A_out) std::memcpy(A_out, A.data(), A.size() * sizeof(cpx<double>));
+    if (Ainv_out) std::memcpy(Ainv_out, L.Ainv.data(), L.Ainv.size() * sizeof(cpx<double>));
+    if (Llow) {
+        const int T = c.dims[3];
+        TmpBuf M;
+        M.alloc((size_t)T * nk * nk * sizeof(double2));
+        timeslice_dots(c, X.data(), nk, X.data(), nk, M.p);
+        std::vector<cpx<double>> Mh((size_t)T * nk * nk);
+        MG_CUDA(cudaMemcpyAsync(Mh.data(), M.p, Mh.size() * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+        sync(c);
+        for (int t = 0; t < T; ++t) {
+            cpx<double> acc;
+            for (int j = 0; j < nk; ++j)
+                for (int i = 0; i < nk; ++i)
+                    acc = acc + L.Ainv[(size_t)i * nk + j] * Mh[((size_t)t * nk + j) * nk + i];
+            Llow[2 * t] = acc.re;
+            Llow[2 * t + 1] = acc.im;
+        }
+    }
+}
+
+// mode 0: y = Q~^-1_low x ; mode 1: y = R~ x  (FP64 internal spinors, y != x)
+void lma_apply(Ctx &c, int mode, const void *x64, void *y64) {
+    MG_REQUIRE(c.lma && (mode == 0 || mode == 1), MGEIG_ENOTSETUP);
+    Lma &L = *c.lma;
+    const size_t N = c.fine_ncpx();
+    const int nk = L.n;
+    if (mode == 0) blas_zero<double>(c, y64, N);
+    else blas_copy<double>(c, x64, y64, N);
+    if (!nk) return;
+    std::vector<const void *> X(L.V.begin(), L.V.end());
+    blas_multidot<double>(c, X.data(), nk, x64, N, dslot(c, H1));
+    fetch(c, H1 + nk);
+    std::vector<cpx<double>> coef(nk);
+    for (int i = 0; i < nk; ++i) {
+        cpx<double> acc;
+        for (int j = 0; j < nk; ++j) acc = acc + L.Ainv[(size_t)i * nk + j] * *hslot(c, H1 + j);
+        coef[i] = acc;
+    }
+    std::vector<const void *> B(mode == 0 ? L.V.begin() : L.QV.begin(), mode == 0 ? L.V.end() : L.QV.end());
+    blas_multi_axpy<double>(c, y64, B.data(), nk, upload(c, coef), mode == 0 ? 1.0 : -1.0, N);
+}
+
+// L_high(t) = 1/nstoch sum_n sum_{x in t} <eta_n(x) | s_n(x)>, Q s_n = R~ eta_n
+void lma_loop_high(Ctx &c, int nstoch, uint64_t seed, double tol, double *Lhigh, int *outer_iters) {
+    MG_REQUIRE(c.lma, MGEIG_ENOTSETUP);
+    const int T = c.dims[3];
+    TmpBuf eta, b, sv, M;
+    eta.alloc(f64_bytes(c) * nstoch);
+    b.alloc(f64_bytes(c));
+    sv.alloc(f64_bytes(c));
+    M.alloc((size_t)T * sizeof(double2));
+    z2_spinors(c, seed, eta.p, nstoch, 0x5EED0002u);
+    std::vector<double> acc(2 * T, 0.0);
+    std::vector<double2> Mh(T);
+    const int outer0 = c.st.outer_iters;
+    for (int k = 0; k < nstoch; ++k) {
+        const void *ek = eta.as<char>() + f64_bytes(c) * k;
+        lma_apply(c, 1, ek, b.p);
+        const int rc = fgmres_solve(c, 0.0, b.p, sv.p, tol);
+        MG_REQUIRE(rc == MGEIG_OK, rc);
+        const void *X[1] = {ek};
+        const void *Y[1] = {sv.p};
+        timeslice_dots(c, X, 1, Y, 1, M.p);
+        MG_CUDA(cudaMemcpyAsync(Mh.data(), M.p, T * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+        sync(c);
+        for (int t = 0; t < T; ++t) { acc[2 * t] += Mh[t].x; acc[2 * t + 1] += Mh[t].y; }
+    }
+    for (int t = 0; t < 2 * T; ++t) Lhigh[t] = acc[t] / nstoch;
+    if (outer_iters) *outer_iters = c.st.outer_iters - outer0;
 }
 
 // ---------------------------------------------------------------------------

@@ -76,3 +76,45 @@ def test_fgmres_solve_matches_dense(ref):
     assert np.linalg.norm(A @ x.ravel() - b.ravel()) <= 1.05e-10 * np.linalg.norm(b)
     xs = np.linalg.solve(A, b.ravel())
     assert np.linalg.norm(x.ravel() - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_non_hermitian_d_solve_matches_dense(ref, precision):
+    """(D - sigma gamma5) x = b, sigma = 0 (the Wilson-clover system) and 0.1,
+    against numpy.linalg.solve of the dense D_sigma = gamma5 (Q - sigma)."""
+    from paper_1509_06865_gb300 import Context
+    from oracle import dirac
+    U, op, Qm, w, v = ref
+    c = DENSE4
+    ctx = Context(c["dims"])
+    ctx.set_params(m0=c["m0"], csw=c["csw"], agg=(2, 2, 2, 2), n_tv=8, sap_block=(2, 2, 2, 2), precision=precision)
+    ctx.load_gauge(U)
+    ctx.setup(5)
+    b = synth.z2_noise(c["dims"], 1, 4)[0]
+    g5 = np.tile(dirac.GAMMA5_DIAG.repeat(3), Qm.shape[0] // 12)
+    for sigma in (0.0, 0.1):
+        x, st = ctx.solve_d(b, sigma, 1e-10)
+        assert st["converged"], st
+        Dm = g5[:, None] * (Qm - sigma * np.eye(Qm.shape[0]))
+        assert np.linalg.norm(Dm @ x.ravel() - b.ravel()) <= 1.05e-10 * np.linalg.norm(b)
+        xs = np.linalg.solve(Dm, b.ravel())
+        assert np.linalg.norm(x.ravel() - xs) <= 1e-8 * np.linalg.norm(xs)
+        # and the oracle's stencil form of D_sigma
+        assert dirac.norm(op.D_sigma(x, sigma) - b) <= 1.05e-10 * dirac.norm(b)
+    ctx.close()
+
+
+def test_p_from_a_subset_of_the_modes(ref):
+    """P built from the first 2 iterated vectors and the setup's other 6 test
+    vectors (p_modes = 2): the same 4 lowest pairs as dense eigh."""
+    from paper_1509_06865_gb300 import Context
+    U, op, Qm, w, v = ref
+    c = DENSE4
+    ctx = Context(c["dims"])
+    ctx.set_params(m0=c["m0"], csw=c["csw"], agg=(2, 2, 2, 2), n_tv=8, sap_block=(2, 2, 2, 2), p_modes=2)
+    ctx.load_gauge(U)
+    ctx.setup(c["seed"])
+    lam, V, res, st = ctx.eigensolve(c["n_eig"], 1e-10)
+    ctx.close()
+    assert st["converged"] and np.all(res <= 1e-10), st
+    assert np.abs(lam - w[:c["n_eig"]]).max() <= 1e-10 * np.abs(w[:c["n_eig"]]).max()
