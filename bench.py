@@ -594,6 +594,43 @@ def neig_study(device=0):
 
 
 # ---------------------------------------------------------------------------
+# batched shifted solves of several fields (the batched workload: 16 shifts in
+# [0, 0.05] x 12 Z2 + iZ2 right-hand sides per field; fields of three sizes)
+
+
+def batch_study(device=0, nrhs=12, nsig=16):
+    import torch
+
+    import synth
+    from paper_1509_06865_gb300 import MIXED, Context, solve_batch
+
+    fields = [((8, 8, 8, 8), 1101), ((8, 8, 8, 8), 1102), ((16, 16, 16, 32), 1103), ((16, 16, 16, 32), 1104)]
+    ctxs, rhs = [], []
+    for dims, seed in fields:
+        ctx = Context(dims, device=device)
+        # m0 above the critical value of the 16^3x32 workload: min |lambda| > max sigma (no singular system)
+        ctx.set_params(m0=load_m0() + 0.06, csw=1.9, n_tv=20, precision=MIXED)
+        ctx.load_gauge(synth.gauge_field(dims, 0.2, seed))
+        ctx.setup(seed)
+        ctxs.append(ctx)
+        rhs.append(synth.z2_noise(dims, nrhs, seed))
+    sigmas = [0.05 * k / (nsig - 1) for k in range(nsig)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xs, st = solve_batch(ctxs, sigmas, rhs, 1e-10)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nsys = len(fields) * nsig * nrhs
+    out = dict(fields=[list(d) for d, _ in fields], shifts=nsig, rhs_per_field=nrhs, systems=nsys, s=dt,
+               systems_per_s=nsys / dt, converged=st["converged"], outer_iters=st["outer_iters"],
+               mean_outer_per_system=st["outer_iters"] / nsys, note="host buffers in and out, tol 1e-10")
+    for ctx in ctxs:
+        ctx.close()
+    print(json.dumps(out), flush=True)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # small self-terminating cases for ncu (one GPU, a few GB)
 
 
@@ -648,6 +685,8 @@ def main():
     ap.add_argument("--profile-case", choices=["eig16", "stencil32"])
     ap.add_argument("--neig-study", action="store_true",
                     help="time Algorithm 1 on the 16^3x32 field for 4..32 wanted pairs and with P from 12 / 6 modes")
+    ap.add_argument("--batch-study", action="store_true",
+                    help="16 shifts x 12 Z2 right-hand sides on four fields (8^4, 16^3x32) with mgeig_solve_batch")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
@@ -658,6 +697,9 @@ def main():
         return
     if args.neig_study:
         neig_study()
+        return
+    if args.batch_study:
+        batch_study()
         return
     if args.impl == "reference":
         run_reference(args)

@@ -79,8 +79,6 @@ struct CGArgs {
     int rb;                        // rows per block (the last block may own fewer)
     int nslice;                    // owned-row vectors per block: V (m+1), U (m+1), rhs, x, w
     int smem_slices, smem_defl;    // 1: the slices / copies of W, A W live in shared memory
-    int xstage;                    // > 0: shared-memory offset (elements) of the staged neighbour vectors, + 1
-    int defl_off;                  // shared-memory offset (elements) of the W, A W copies
     const cpx<R> *Dc;              // [9][nagg][col][row]
     const void *L16;               // 16-bit links [9][nagg][re|im][row][col] (16-bit kernels)
     const float *Ls;               // their scales [9][nagg]
@@ -143,28 +141,10 @@ __device__ __forceinline__ cpx<double> ldcg(const cpx<double> *p) {
 // hop blocks, and the group reduces with shuffles.
 constexpr int TPR = 8;
 
-// The neighbour vectors of the block's rows: xs[((site - s_lo) * 9 + d) * n2 + j] =
-// v[nbr(d, site) * n2 + j] for the sites s_lo .. of the rows [r0, r1); direction 0
-// is the site itself.  40 rows of a site read the same nine neighbour vectors, so
-// staging them once replaces those L2 re-reads by shared-memory reads.
 template <typename R>
-__device__ __forceinline__ void stage_neighbours(const CGArgs<R> &a, const cpx<R> *v, cpx<R> *xs, int r0, int r1) {
-    const int n2 = 2 * a.ntv;
-    const int s_lo = r0 / n2, ns = (r1 - 1) / n2 - s_lo + 1;
-    for (int e = threadIdx.x; e < ns * 9 * n2; e += blockDim.x) {
-        const int j = e % n2, d = (e / n2) % 9, sl = e / (9 * n2);
-        const int nb = __ldg(a.nbr + (size_t)d * a.nagg + s_lo + sl);
-        xs[e] = ldcg(v + (size_t)nb * n2 + j);
-    }
-    __syncthreads();
-}
-
-template <typename R>
-__device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1,
-                                        const cpx<R> *xs) {
+__device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1) {
     const int n2 = 2 * a.ntv;
     const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
-    const int s_lo = r0 / n2;
     for (int tb = r0; tb < r1; tb += ngrp) {
         const int t = tb + grp;
         cpx<R> acc0, acc1;
@@ -175,14 +155,14 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
                 // loaded before they are used, so their L2 latencies overlap
                 constexpr int U = (2 * CG_MAXK + TPR - 1) / TPR;
                 for (int d = 0; d < 9; ++d) {
+                    const int nb = __ldg(a.nbr + (size_t)d * a.nagg + site);
                     const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
-                    const cpx<R> *xb = xs ? xs + ((size_t)(site - s_lo) * 9 + d) * n2
-                                          : v + (size_t)__ldg(a.nbr + (size_t)d * a.nagg + site) * n2;
+                    const cpx<R> *xb = v + (size_t)nb * n2;
                     cpx<R> bv[U], xv[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         const int j = q + u * TPR;
-                        if (j < n2) { bv[u] = blk[(size_t)j * n2]; xv[u] = xs ? xb[j] : ldcg(xb + j); }
+                        if (j < n2) { bv[u] = blk[(size_t)j * n2]; xv[u] = ldcg(xb + j); }
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u)
@@ -191,16 +171,15 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
             } else {
 #pragma unroll 3
                 for (int d = 0; d < 9; ++d) {
+                    const int nb = __ldg(a.nbr + (size_t)d * a.nagg + site);
                     const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
-                    const cpx<R> *xb = xs ? xs + ((size_t)(site - s_lo) * 9 + d) * n2
-                                          : v + (size_t)__ldg(a.nbr + (size_t)d * a.nagg + site) * n2;
-                    auto X = [&](int j) { return xs ? xb[j] : ldcg(xb + j); };
+                    const cpx<R> *xb = v + (size_t)nb * n2;
                     int j = q;
                     for (; j + TPR < n2; j += 2 * TPR) {
-                        cmac(acc0, blk[(size_t)j * n2], X(j));
-                        cmac(acc1, blk[(size_t)(j + TPR) * n2], X(j + TPR));
+                        cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
+                        cmac(acc1, blk[(size_t)(j + TPR) * n2], ldcg(xb + j + TPR));
                     }
-                    if (j < n2) cmac(acc0, blk[(size_t)j * n2], X(j));
+                    if (j < n2) cmac(acc0, blk[(size_t)j * n2], ldcg(xb + j));
                 }
             }
         }
@@ -211,8 +190,7 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
         }
         if (t < r1 && q == 0) {
             if ((t % n2) >= a.ntv) acc = -acc;
-            const cpx<R> vt = xs ? xs[((size_t)(t / n2 - s_lo) * 9) * n2 + t % n2] : ldcg(v + t);
-            out[t - r0] = s * acc - (a.sigma * s) * vt;
+            out[t - r0] = s * acc - (a.sigma * s) * ldcg(v + t);
         }
     }
 }
@@ -222,10 +200,9 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
 // hop block's sum is multiplied by the block's scale.
 template <typename H>
 __device__ __forceinline__ void qmatvec16(const CGArgs<float> &a, const cpx<float> *v, float s, cpx<float> *out,
-                                          int r0, int r1, const cpx<float> *xs) {
+                                          int r0, int r1) {
     using HP = typename H16<H>::P;
     const int n2 = 2 * a.ntv, np = a.ntv;
-    const int s_lo = r0 / n2;
     const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
     constexpr int U = (CG_MAXK + TPR - 1) / TPR;   // pairs per lane (n2 / 2 <= CG_MAXK)
     const H *L = static_cast<const H *>(a.L16);
@@ -236,16 +213,16 @@ __device__ __forceinline__ void qmatvec16(const CGArgs<float> &a, const cpx<floa
             const int site = t / n2, row = t % n2;
             for (int d = 0; d < 9; ++d) {
                 const size_t blk = (size_t)d * a.nagg + site;
+                const int nb = __ldg(a.nbr + blk);
                 const HP *pr = reinterpret_cast<const HP *>(L + blk * 2 * n2 * n2 + (size_t)row * n2);
                 const HP *pi = pr + (size_t)n2 * n2 / 2;
-                const float4 *xb = reinterpret_cast<const float4 *>(
-                    xs ? xs + ((size_t)(site - s_lo) * 9 + d) * n2 : v + (size_t)__ldg(a.nbr + blk) * n2);
+                const float4 *xb = reinterpret_cast<const float4 *>(v + (size_t)nb * n2);
                 HP rv[U], iv[U];
                 float4 xv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int p = q + u * TPR;
-                    if (p < np) { rv[u] = pr[p]; iv[u] = pi[p]; xv[u] = xs ? xb[p] : __ldcg(xb + p); }
+                    if (p < np) { rv[u] = pr[p]; iv[u] = pi[p]; xv[u] = __ldcg(xb + p); }
                 }
                 float dr = 0.f, di = 0.f;
 #pragma unroll
@@ -271,8 +248,7 @@ __device__ __forceinline__ void qmatvec16(const CGArgs<float> &a, const cpx<floa
         if (t < r1 && q == 0) {
             cpx<float> acc(ar, ai);
             if ((t % n2) >= a.ntv) acc = -acc;
-            const cpx<float> vt = xs ? xs[((size_t)(t / n2 - s_lo) * 9) * n2 + t % n2] : ldcg(v + t);
-            out[t - r0] = s * acc - (a.sigma * s) * vt;
+            out[t - r0] = s * acc - (a.sigma * s) * ldcg(v + t);
         }
     }
 }
@@ -280,12 +256,9 @@ __device__ __forceinline__ void qmatvec16(const CGArgs<float> &a, const cpx<floa
 // the product of the kernel's link format LK (0: level precision, 1: BF16, 2: FP16)
 template <typename R, int LK>
 __device__ __forceinline__ void matvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1) {
-    extern __shared__ __align__(16) unsigned char cg_dyn[];
-    cpx<R> *xs = a.xstage ? reinterpret_cast<cpx<R> *>(cg_dyn) + (a.xstage - 1) : nullptr;
-    if (xs) stage_neighbours<R>(a, v, xs, r0, r1);
-    if constexpr (LK == 0) qmatvec<R>(a, v, s, out, r0, r1, xs);
-    else if constexpr (LK == 1) qmatvec16<__nv_bfloat16>(a, v, s, out, r0, r1, xs);
-    else qmatvec16<__half>(a, v, s, out, r0, r1, xs);
+    if constexpr (LK == 0) qmatvec<R>(a, v, s, out, r0, r1);
+    else if constexpr (LK == 1) qmatvec16<__nv_bfloat16>(a, v, s, out, r0, r1);
+    else qmatvec16<__half>(a, v, s, out, r0, r1);
 }
 
 // Scalars (partial sums, Hessenberg matrix, Givens rotations, E^-1) are kept in
@@ -329,7 +302,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     cpx<R> *rhs = S + (size_t)(2 * m + 2) * rb;
     cpx<R> *xs = rhs + rb;
     cpx<R> *ws = xs + rb;
-    cpx<R> *Dl = a.smem_defl ? reinterpret_cast<cpx<R> *>(cg_dyn) + a.defl_off : nullptr;
+    cpx<R> *Dl = a.smem_defl ? reinterpret_cast<cpx<R> *>(cg_dyn) + (size_t)a.nslice * rb : nullptr;
     auto Wv = [&](int l) -> const cpx<R> * { return Dl ? Dl + (size_t)l * rb : a.W + (size_t)l * a.n + r0; };
     auto AWv = [&](int l) -> const cpx<R> * { return Dl ? Dl + (size_t)(k + l) * rb : a.AW + (size_t)l * a.n + r0; };
     auto g5 = [&](int i, cpx<R> v) { return ((r0 + i) % n2) >= a.ntv ? -v : v; };
@@ -661,8 +634,6 @@ namespace {
 struct CGPlan {
     int G, rb, nslice, m;
     bool smem_slices, smem_defl;
-    int xstage;               // shared-memory offset of the staged neighbours (elements) + 1, or 0
-    size_t defl_off;          // shared-memory offset of the W, A W copies (elements)
     size_t dyn_smem;          // dynamic shared memory per block
     size_t off_slices, off_partial, scratch_bytes;   // global scratch layout
 };
@@ -700,17 +671,9 @@ CGPlan compute_plan(Ctx &c, int k) {
     p.nslice = 2 * (p.m + 1) + 3;
     const size_t budget = CG_SMEM_LIMIT > fa.sharedSizeBytes ? CG_SMEM_LIMIT - fa.sharedSizeBytes : 0;
     const size_t slice_b = (size_t)p.nslice * p.rb * elem, defl_b = (size_t)2 * k * p.rb * elem;
-    // the neighbour vectors of the block's rows (they span at most (rb - 1) / n2 + 2 sites)
-    const int n2 = 2 * c.prm.n_tv;
-    const size_t xst_b = (size_t)((p.rb - 1) / n2 + 2) * 9 * n2 * elem;
-    // priority: the slices, then the staged neighbours, then the copies of W, A W
     p.smem_slices = slice_b <= budget;
-    const size_t used = p.smem_slices ? slice_b : 0;
-    p.xstage = used + xst_b <= budget ? (int)(used / elem) + 1 : 0;
-    const size_t used2 = used + (p.xstage ? xst_b : 0);
-    p.smem_defl = p.smem_slices && k > 0 && used2 + defl_b <= budget;
-    p.dyn_smem = used2 + (p.smem_defl ? defl_b : 0);
-    p.defl_off = used2 / elem;
+    p.smem_defl = p.smem_slices && k > 0 && slice_b + defl_b <= budget;
+    p.dyn_smem = p.smem_slices ? slice_b + (p.smem_defl ? defl_b : 0) : 0;
     // global scratch: pub | slices (when not in shared memory) | partial sums
     p.off_slices = align256((size_t)n * elem);
     p.off_partial = p.off_slices + (p.smem_slices ? 0 : align256((size_t)p.G * slice_b));
@@ -764,8 +727,7 @@ void coarse_gmres_at(Ctx &c, double sigma, const void *rc, void *ec, void *scrat
     CGArgs<R> a;
     a.nagg = c.nagg; a.ntv = c.prm.n_tv; a.n = c.nagg * 2 * c.prm.n_tv;
     a.rb = p.rb; a.nslice = p.nslice;
-    a.smem_slices = p.smem_slices; a.smem_defl = p.smem_defl; a.xstage = p.xstage;
-    a.defl_off = (int)p.defl_off;
+    a.smem_slices = p.smem_slices; a.smem_defl = p.smem_defl;
     a.Dc = static_cast<const cpx<R> *>(c.Dc.p);
     a.L16 = c.Dc16.p;
     a.Ls = c.Dcs.as<float>();
