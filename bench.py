@@ -37,7 +37,6 @@ WORKLOAD = dict(
              "20 lowest eigenpairs of Q to resid 1e-10; 2-level MG (4^4 aggregates, 20 test vectors, SAP 4^4)",
     dims=[16, 16, 16, 32], eps=0.2, seed=1002, csw=1.9, n_eig=20, tol=1e-10,
 )
-ORACLE_WORK = os.path.join(ROOT, "tests", "golden", "oracle_work_8x8x8x16.json")
 # library timer classes that are one kernel each (the BLAS classes are several)
 SINGLE_KERNEL_CLASSES = ("coarse_gmres", "stencil_f64", "stencil_f32", "sap_f32", "sap_f64", "restrict", "prolong",
                          "coarse_apply", "coarse_build", "interp_build")
@@ -164,7 +163,7 @@ def stencil_microbench(ctx, dims, flush, peak_hbm, n=40, nrhs=0):
     import torch
 
     import synth
-    from paper_1509_06865_gb300 import OP_Q, PREC_F32, PREC_F64
+    from paper_1509_06865_gb300 import OP_Q, PREC_F32, PREC_F32_F64_DS, PREC_F64, PREC_F64_DS
 
     V = int(np.prod(dims))
     s = torch.cuda.ExternalStream(ctx.stream())
@@ -197,6 +196,18 @@ def stencil_microbench(ctx, dims, flush, peak_hbm, n=40, nrhs=0):
         gbs = per_site * V / (ms * 1e-3) / 1e9
         out[name] = dict(ms=ms, gbs=gbs, frac_hbm=gbs / peak_hbm, bytes_per_site=per_site,
                          gflops=1872.0 * V / (ms * 1e-3) / 1e9)
+        if prec == PREC_F64:
+            # the mixed solver's FP64-output stencil in double-float arithmetic:
+            # FP64 in (x 192 B), and FP32 in (x 96 B, the outer FGMRES matvec);
+            # links and clover as float pairs (the FP64 byte counts)
+            x32 = ctx.alloc_dev(V * 12 * 8)
+            ctx.pack_spinors(x_host, x32, PREC_F32)
+            for dprec, dname, xin in ((PREC_F64_DS, "f64_ds", x), (PREC_F32_F64_DS, "f32in_f64_ds", x32)):
+                ms = timeit(lambda: ctx.apply_dev(xin, y, 1e-3, OP_Q, dprec))
+                ps = per_site - (96 if dprec == PREC_F32_F64_DS else 0)
+                gbs = ps * V / (ms * 1e-3) / 1e9
+                out[dname] = dict(ms=ms, gbs=gbs, frac_hbm=gbs / peak_hbm, bytes_per_site=ps,
+                                  flop_per_site=1872, speedup_vs_f64=out["f64"]["ms"] / ms)
     if nrhs > 0:
         nbytes = V * 12 * 8
         x = ctx.alloc_dev(nbytes * nrhs)
@@ -318,8 +329,8 @@ def run_gpu(args):
 
     # the 20 lowest pairs of the 32^3 x 64 field (one step each, after the timed region)
     north = None if args.no_north_star else north_star(args, flush, local)
-    # like for like: the GPU eigensolve of the 8^3 x 16 field on which the oracle's
-    # complete eigensolve was timed
+    # like for like: the GPU eigensolve of the 4^4 field on which the CPU baseline
+    # times the oracle's complete eigensolve
     small = small_field(flush, local)
 
     if rank != 0:
@@ -341,7 +352,7 @@ def run_gpu(args):
                     sweeps=st["sweeps"], solves=st["solves"], outer_iters=st["outer_iters"],
                     mg_cycles=st["mg_cycles"], coarse_iters=st["coarse_iters"]),
         north_star_32x32x32x64=north,
-        like_for_like_8x8x8x16=small,
+        like_for_like_4x4x4x4=small,
         alu_peaks=alu,
         stencil=dict(sten, l2="flushed before every launch", lattice=w["dims"],
                      lattice_32x32x32x64=sten_big),
@@ -361,6 +372,10 @@ def run_gpu(args):
     )
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline_subprocess()
+        cs = line["cpu_baseline"].get("complete_4x4x4x4")
+        if cs:
+            small["oracle_s"] = cs["wall_s"]
+            small["oracle_over_gpu"] = cs["wall_s"] / small["gpu_s"]
     print(json.dumps(line), flush=True)
 
 
@@ -407,123 +422,128 @@ def north_star(args, flush, device):
 
 
 def small_field(flush, device):
-    """The 20 lowest pairs of the 8^3 x 16 field (mixed), the field of the oracle's
-    complete timed eigensolve (tests/golden/oracle_work_8x8x8x16.json)."""
+    """The 4 lowest pairs of the 4^4 workload (mixed, to 1e-10), the field of the
+    oracle's complete eigensolve in the CPU baseline: the like-for-like ratio of
+    two complete runs."""
     import torch
 
     import synth
     from paper_1509_06865_gb300 import MIXED, Context
 
-    cfg = workload("check_8x8x8x16")
+    cfg = workload("dense_4x4x4x4")
     dims = tuple(cfg["dims"])
     U = synth.gauge_field(dims, cfg["eps"], cfg["seed"])
-    ctx = Context(dims, device=device)
-    ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
-                   sap_block=cfg["sap_block"], precision=MIXED)
-    flush.fill_(5)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    ctx.load_gauge(U)
-    ctx.setup(cfg["seed"])
-    lam, _, res, st = ctx.eigensolve(cfg["n_eig"], cfg["tol"], want_vectors=False)
-    e1.record()
-    torch.cuda.synchronize()
-    ctx.close()
-    out = dict(gpu_s=e0.elapsed_time(e1) / 1e3, max_resid=float(max(res)), converged=st["converged"])
-    if os.path.exists(ORACLE_WORK):
-        with open(ORACLE_WORK) as f:
-            ow = json.load(f)
-        out.update(oracle_s=ow["wall_s"], oracle_cores=ow["host_cores_used"],
-                   oracle_host="the container that ran tests/golden/make_golden.py (x86-64), not the GPU box",
-                   oracle_over_gpu=ow["wall_s"] / out["gpu_s"])
-    return out
+    times = []
+    for _ in range(3):
+        ctx = Context(dims, device=device)
+        ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
+                       sap_block=cfg["sap_block"], precision=MIXED)
+        flush.fill_(5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.load_gauge(U)
+        ctx.setup(cfg["seed"])
+        lam, _, res, st = ctx.eigensolve(cfg["n_eig"], cfg["tol"], want_vectors=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.close()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return dict(gpu_s=statistics.median(times), max_resid=float(max(res)), converged=st["converged"],
+                n_eig=cfg["n_eig"], outer_iters=st["outer_iters"], solves=st["solves"])
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and --impl reference)
 
 
-def oracle_prices():
-    """Live oracle time of every operation the oracle's eigensolve performs, on
-    the 16^3 x 32 benchmark field (the coarse-operator build on the 8^3 x 16
-    field, scaled by the volume ratio: its work is per site)."""
+def oracle_outer_iteration_s(name: str, iters: int):
+    """Seconds per outer FGMRES iteration of the oracle on a workload's field: one
+    two-grid cycle (the coarse GMRES at its iteration cap, the SAP cycles), one
+    FP64 application of Q - sigma and the Arnoldi Gram-Schmidt step, timed over
+    `iters` iterations of one shifted solve (sigma = 0, P from the workload's
+    number of Philox-uniform test vectors; building P and the coarse operator is
+    not timed)."""
     import numpy as np
 
     import synth
-    from oracle import dirac, mg
+    from oracle import dirac, krylov, mg
 
-    w = WORKLOAD
-    dims = tuple(w["dims"])
-    U = synth.gauge_field(dims, w["eps"], w["seed"])
-    t = {}
-
-    def clock(name, fn, reps=1):
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            r = fn()
-        t[name] = (time.perf_counter() - t0) / reps
-        return r
-
-    op = clock("clover", lambda: dirac.WilsonClover(U, load_m0(), w["csw"]))
-    x, y = synth.gaussian_vectors(dims, 2, 1)
-    clock("fine_D", lambda: op.D(x))
-    clock("fine_vdot_axpy", lambda: y + complex(np.vdot(x, y)) * x, reps=4)
-    sap = mg.SAP(op, (4, 4, 4, 4))
-    clock("sap_cycle", lambda: sap.smooth(y, x, 1e-3, 1, 4))
-    Wt = synth.uniform_vectors(dims, 20, 5)
-    P = clock("interp_build", lambda: mg.Interpolation(Wt, (4, 4, 4, 4)))
-    rc = clock("restrict", lambda: P.restrict(x))
-    clock("prolong", lambda: P.prolong(rc))
-    C = mg.CoarseOperator(np.zeros((9, P.nagg, 40, 40), dtype=np.complex128), P.cdims, 20)
-    clock("coarse_apply", lambda: C.apply(rc, 1e-3), reps=4)
-    small = (8, 8, 8, 16)
-    Us = synth.gauge_field(small, w["eps"], w["seed"])
-    ops = dirac.WilsonClover(Us, load_m0(), w["csw"])
-    Ps = mg.Interpolation(synth.uniform_vectors(small, 20, 5), (4, 4, 4, 4))
-    clock("coarse_build_8x8x8x16", lambda: mg.coarse_operator(ops, Ps))
-    t["coarse_build"] = t["coarse_build_8x8x8x16"] * int(np.prod(dims)) / int(np.prod(small))
-    # one SAP cycle applies D_sigma ten times (residual + 4 MR steps, two colours);
-    # those are counted with the stencil applications
-    t["sap_cycle_rest"] = max(0.0, t["sap_cycle"] - 10 * t["fine_D"])
-    return t
+    cfg = workload(name)
+    dims = tuple(cfg["dims"])
+    U = synth.gauge_field(dims, cfg["eps"], cfg["seed"])
+    m0 = cfg["m0"] if cfg.get("m0") is not None else load_m0()
+    op = dirac.WilsonClover(U, m0, cfg["csw"], tuple(cfg.get("bc", (1, 1, 1, 1))))
+    params = dict(mg.DEFAULT_PARAMS, agg=tuple(cfg["agg"]), ntv=cfg["n_tv"], sap_block=tuple(cfg["sap_block"]),
+                  coarse_tol=0.0)
+    # the two-grid preconditioner with a seeded random coarse operator of the
+    # right shape: at a fixed coarse iteration count its cost does not depend on
+    # the operator's values, and the oracle's Galerkin build (minutes at 16^3 x 32)
+    # is not part of an outer iteration
+    W = synth.uniform_vectors(dims, cfg["n_tv"], cfg["seed"])
+    B = object.__new__(mg.TwoGrid)
+    B.op, B.p, B.W, B._defl = op, params, np.array(W), None
+    B.P = mg.Interpolation(B.W, params["agg"])
+    n2 = 2 * cfg["n_tv"]
+    rng = np.random.default_rng(cfg["seed"])
+    B.Dc = rng.standard_normal((9, B.P.nagg, n2, n2)) + 1j * rng.standard_normal((9, B.P.nagg, n2, n2))
+    B.coarse = mg.CoarseOperator(B.Dc, B.P.cdims, B.P.ntv)
+    B.sap = mg.SAP(op, params["sap_block"])
+    b = synth.gaussian_vectors(dims, 1, 3)[0]
+    B(b, 0.0)   # the coarse deflation data, outside the timed region
+    t0 = time.perf_counter()
+    krylov.fgmres(lambda v: op.Q_sigma(v, 0.0), lambda v: B(v, 0.0), b, tol=0.0, restart=iters, maxiter=iters)
+    return (time.perf_counter() - t0) / iters
 
 
-def oracle_baseline():
-    """The oracle's own operation counts of a complete 20-pair eigensolve (the
-    8^3 x 16 field of the same generator, run to 1e-10 by
-    tests/golden/make_golden.py, which calls only oracle/), each priced by its
-    live oracle time on the 16^3 x 32 field.  The counts of a multigrid
-    eigensolve hardly depend on the volume (the premise of the method), the
-    price of each operation grows with it.  Returns the s per 20 eigenpairs and
-    how it was obtained; `cores` is the CPU time of the sample over its wall
-    time (numpy's element-wise kernels run on one core)."""
+def oracle_complete_small():
+    """One complete oracle eigensolve (setup and Algorithm 1 with the library's
+    default additions) of the 4^4 workload's 4 lowest pairs to 1e-10: its wall
+    time and work."""
+    import numpy as np
+
+    import synth
+    from oracle import dirac, mg, rqi
+
+    cfg = workload("dense_4x4x4x4")
+    dims = tuple(cfg["dims"])
+    U = synth.gauge_field(dims, cfg["eps"], cfg["seed"])
+    t0 = time.perf_counter()
+    op = dirac.WilsonClover(U, cfg["m0"], cfg["csw"])
+    params = dict(mg.DEFAULT_PARAMS, agg=tuple(cfg["agg"]), ntv=cfg["n_tv"], sap_block=tuple(cfg["sap_block"]))
+    lam, V, res, st = rqi.eigensolve(op, synth.uniform_vectors(dims, cfg["n_tv"], cfg["seed"]), cfg["n_eig"],
+                                     cfg["tol"], params)
+    wall = time.perf_counter() - t0
+    assert float(np.max(res)) <= cfg["tol"], res
+    return dict(wall_s=wall, n_eig=cfg["n_eig"], sweeps=st["sweeps"], solves=st["solves"],
+                outer_iters=st["outer_iters"], max_res=float(np.max(res)))
+
+
+def oracle_baseline(c_big=None):
+    """The FP64 CPU oracle, measured: a complete oracle eigensolve of the 4^4
+    workload (4 pairs to 1e-10, about 40 s), scaled to the 20 pairs of the 16^3 x
+    32 benchmark field by the oracle's own measured cost of one outer FGMRES
+    iteration on both fields (about 20 s on the large one) and the pair count:
+        value = T(4^4, complete) * C(16^3x32) / C(4^4) * 20 / 4.
+    The premise is the method's: outer iterations per eigenpair hardly depend on
+    the volume (the paper's Fig. 1), the cost of each grows with it.  `cores` is
+    the CPU time of the sample over its wall time (numpy's element-wise kernels
+    use one core, its LAPACK calls more)."""
     c0 = time.process_time()
     t0 = time.perf_counter()
-    price = oracle_prices()
+    small = oracle_complete_small()
+    c_small = oracle_outer_iteration_s("dense_4x4x4x4", 6)
+    if c_big is None:
+        c_big = oracle_outer_iteration_s("bench_16x16x16x32", 1)
     wall = time.perf_counter() - t0
     cores = (time.process_time() - c0) / wall
-    with open(ORACLE_WORK) as f:
-        work = json.load(f)
-    n = work["counts"]
-    parts = dict(
-        stencil=n["fine_D_vectors"] * price["fine_D"],
-        sap_rest=n["sap_cycles"] * price["sap_cycle_rest"],
-        coarse_build=n["coarse_builds"] * price["coarse_build"],
-        interp_build=n["interp_builds"] * price["interp_build"],
-        restrict=n["restricts"] * price["restrict"],
-        prolong=n["prolongs"] * price["prolong"],
-        coarse_apply=n["coarse_applies"] * price["coarse_apply"],
-        fine_blas=n["fine_vdots"] * price["fine_vdot_axpy"],
-        clover=price["clover"],
-    )
-    return dict(value=sum(parts.values()), unit="s", cores=round(cores, 2), nproc=os.cpu_count(), kind="oracle",
-                sample="live FP64 oracle timings on the 16^3x32 field of one of each operation (Wilson-clover D, "
-                       "an SAP cycle, P from 20 test vectors, restriction, prolongation, a coarse apply, a fine "
-                       "vdot+axpy, the clover term; the coarse-operator build on the 8^3x16 field scaled by volume) "
-                       "x the operation counts of the oracle's own complete 20-pair eigensolve of the 8^3x16 field "
-                       f"({work['wall_s']:.0f} s wall there, tests/golden/oracle_work_8x8x8x16.json)",
-                sample_seconds=wall, parts_s=parts, prices_s=price, counts=n)
+    big_pairs = WORKLOAD["n_eig"]
+    value = small["wall_s"] * (c_big / c_small) * (big_pairs / small["n_eig"])
+    return dict(value=value, unit="s", cores=round(cores, 2), nproc=os.cpu_count(), kind="oracle",
+                sample="a complete FP64 oracle eigensolve of the 4^4 workload (4 pairs to 1e-10, wall time measured) "
+                       "scaled to 20 pairs on the 16^3x32 field by the oracle's measured seconds per outer FGMRES "
+                       "iteration on both fields (two-grid cycle + FP64 stencil + Gram-Schmidt) and the pair ratio",
+                sample_seconds=wall, complete_4x4x4x4=small, outer_iteration_s=dict(small=c_small, bench=c_big))
 
 
 def oracle_baseline_subprocess():
@@ -540,10 +560,14 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    # the oracle's cost of one outer iteration on the 16^3 x 32 field (about a
+    # minute with its operator build) is measured once; every warm-up and timed
+    # step runs the complete 4^4 eigensolve and the 4^4 outer-iteration sample
+    c_big = oracle_outer_iteration_s("bench_16x16x16x32", 1)
     for _ in range(args.warmup):
-        oracle_baseline()
+        oracle_baseline(c_big)
     t0 = time.perf_counter()
-    runs = [oracle_baseline() for _ in range(max(1, args.steps))]
+    runs = [oracle_baseline(c_big) for _ in range(max(1, args.steps))]
     elapsed = time.perf_counter() - t0
     v = statistics.median(r["value"] for r in runs)
     last = runs[-1]

@@ -73,6 +73,11 @@ extern "C" {
 /* arithmetic of mgeig_apply */
 #define MGEIG_PREC_F64 0
 #define MGEIG_PREC_F32 1
+/* mgeig_apply_dev only: the mixed solver's FP64-output stencil in double-float
+ * arithmetic (two floats per value, about 2^-46 relative; links and clover
+ * from double-float copies of the FP64 arrays) */
+#define MGEIG_PREC_F64_DS 2       /* x and y FP64                                  */
+#define MGEIG_PREC_F32_F64_DS 3   /* x FP32, y FP64 (the outer FGMRES matvec)      */
 
 /* storage of the coarse operator's links in the mixed-precision preconditioner
  * (spec extension of the Sec. 2.2 precision split: the coarse operator in
@@ -149,6 +154,27 @@ typedef struct mgeig_params {
     double barrier_timeout;   /* seconds (of SM clock) a block of the persistent
                              coarse solver waits at a grid barrier before it gives
                              up, raises MGEIG_ETIMEOUT and returns              */
+    int coarse_blocks;    /* thread blocks of the persistent coarse solver (one
+                             per SM at most, each owning a contiguous slice of
+                             the coarse rows); 0 = one per SM, capped by the
+                             rows.  Fewer blocks make the two grid barriers of an
+                             Arnoldi step cheaper and each block's matvec longer */
+    int blas_ds;          /* 1 (MGEIG_MIXED only): the inner products and vector
+                             updates of the FP64 vectors (Gram-Schmidt and the
+                             Rayleigh quotients of Algorithm 1, the Arnoldi steps
+                             of the outer FGMRES) in double-float arithmetic on
+                             the FP32 pipe, about 2^-46 relative (the compensated
+                             dot product of Ogita, Rump and Oishi); 0: in FP64   */
+    int stencil_ds;       /* 1 (MGEIG_MIXED only): the solver's FP64-output
+                             stencil (the outer FGMRES matvec, residuals,
+                             Rayleigh quotients inside Algorithm 1) in
+                             double-float arithmetic from double-float copies of
+                             the links and clover; 0 (default): in FP64.  The
+                             residuals Algorithm 1 reports are always recomputed
+                             in FP64, and mgeig_apply* with MGEIG_PREC_F64 is
+                             always FP64.  (On GB300 the double-float stencil is
+                             slower than the FP64 one: its long dependent
+                             TwoSum chains at 12 warps per SM are latency bound.) */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */
@@ -217,7 +243,9 @@ int mgeig_apply(mgeig_ctx *ctx, double sigma, int op, int prec,
 /* Same on device memory: x, y are device spinors in the library's internal
  * layout (FP64: double2 [12][V]; FP32: float4 [6][V], component k = 3*spin +
  * colour, float4 q holds components 2q, 2q+1), one field each.  Launched on the
- * context's stream, asynchronous.  For timing the stencil without copies. */
+ * context's stream, asynchronous.  For timing the stencil without copies.
+ * prec may also be MGEIG_PREC_F64_DS or MGEIG_PREC_F32_F64_DS (any context
+ * precision). */
 int mgeig_apply_dev(mgeig_ctx *ctx, double sigma, int op, int prec,
                     const void *x, void *y);
 
@@ -461,6 +489,22 @@ int mgeig_net_loss_grads(mgeig_ctx *ctx, const double *x, const double *t, int b
 /* e = M(r) = ||r|| f(r / ||r||) for one host spinor (computed from its FP32
  * rounding, result widened to FP64). */
 int mgeig_net_apply(mgeig_ctx *ctx, const double *r, double *e);
+
+/* Inner products d_j = <X_j, y> = sum_i conj(X_j[i]) y[i], j < k, of FP64
+   device vectors of n complex values (interleaved re, im, 16-byte aligned): the
+   projection coefficients of the Gram-Schmidt step of Algorithm 1 (Sec. 2.1)
+   and of the Arnoldi process of the outer FGMRES.  X: host array of k device
+   pointers (1 <= k <= 32); y: device pointer; d: host, 2k doubles (re, im).
+   The arithmetic follows the context's params: double-float when blas_ds = 1
+   and precision MGEIG_MIXED, else FP64.  Blocks until d is written.
+   Returns MGEIG_EINVAL for k out of range, n < 1 or a NULL pointer. */
+int mgeig_multidot_dev(mgeig_ctx *ctx, int k, const void *const *X, const void *y, long long n, double *d);
+
+/* y += sum_j c_j X_j, j < k (the update of the same Gram-Schmidt and Arnoldi
+   steps), for the FP64 device vectors of mgeig_multidot_dev; c: host, 2k
+   doubles (re, im).  y must not be one of the X_j.  Same arithmetic rule and
+   errors; returns when y is written. */
+int mgeig_multi_axpy_dev(mgeig_ctx *ctx, int k, const void *const *X, const double *c, void *y, long long n);
 
 /* FMA throughput of the device in FP64 (prec = MGEIG_PREC_F64) or FP32
  * (MGEIG_PREC_F32), in FLOP/s (2 per FMA), measured with the library's own

@@ -60,6 +60,9 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (p.coarse_links != MGEIG_LINKS_LEVEL && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (!(p.barrier_timeout > 0) || !(p.barrier_timeout <= 60)) return MGEIG_EINVAL;
     if (p.p_modes < -1 || p.p_modes == 0) return MGEIG_EINVAL;
+    if (p.coarse_blocks < 0) return MGEIG_EINVAL;
+    if (p.blas_ds != 0 && p.blas_ds != 1) return MGEIG_EINVAL;
+    if (p.stencil_ds != 0 && p.stencil_ds != 1) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES && p.smoother != MGEIG_LEARNED) return MGEIG_EINVAL;
@@ -128,6 +131,9 @@ void mgeig_default_params(mgeig_params *p) {
     p->coarse_links = MGEIG_LINKS_LEVEL;
     p->barrier_timeout = 2.0;
     p->p_modes = -1;
+    p->coarse_blocks = 0;
+    p->blas_ds = 1;
+    p->stencil_ds = 0;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
@@ -182,7 +188,7 @@ void mgeig_destroy(mgeig_ctx *ctx) {
     mg_free(c);
     net_free(c);
     lma_free(c);
-    c.U64.free(); c.U32.free(); c.clov64.free(); c.clov32.free(); c.clov_user.free(); c.staging.free();
+    c.U64.free(); c.U32.free(); c.clov64.free(); c.clov32.free(); c.Uds.free(); c.clovds.free(); c.clov_user.free(); c.staging.free();
     c.red_partial.free(); c.red_out.free(); c.Dc.free(); c.Dc16.free(); c.Dcs.free();
     for (auto &b : c.user_bufs) b.free();
     if (c.pinned) cudaFreeHost(c.pinned);
@@ -365,11 +371,13 @@ int mgeig_apply(mgeig_ctx *ctx, double sigma, int op, int prec, const double *x,
 
 int mgeig_apply_dev(mgeig_ctx *ctx, double sigma, int op, int prec, const void *x, void *y) {
     if (!ctx || !x || !y) return MGEIG_EINVAL;
-    if (check_op(op, prec) != MGEIG_OK) return MGEIG_EINVAL;
+    const bool ds = prec == MGEIG_PREC_F64_DS || prec == MGEIG_PREC_F32_F64_DS;
+    if (check_op(op, ds ? MGEIG_PREC_F64 : prec) != MGEIG_OK) return MGEIG_EINVAL;
     return guarded(ctx, [&](Ctx &c) {
         if (!c.have_gauge) return MGEIG_ENOTSETUP;
         const int mode = op == MGEIG_OP_Q ? MODE_QSIGMA : MODE_DSIGMA;
-        if (prec == MGEIG_PREC_F64) apply_fine<double>(c, mode, sigma, x, y);
+        if (ds) apply_fine_ds(c, mode, sigma, x, y, prec == MGEIG_PREC_F32_F64_DS);
+        else if (prec == MGEIG_PREC_F64) apply_fine_fp64(c, mode, sigma, x, y);
         else apply_fine<float>(c, mode, sigma, x, y);
         return MGEIG_OK;
     });
@@ -828,6 +836,26 @@ int mgeig_net_apply(mgeig_ctx *ctx, const double *r, double *e) {
         net_smooth(c, a32.p, z32.p);
         convert_f32_to_f64(c, z32.p, a.p, c.fine_ncpx());
         internal_to_host(c, a.p, e);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_multidot_dev(mgeig_ctx *ctx, int k, const void *const *X, const void *y, long long n, double *d) {
+    if (!ctx || !X || !y || !d || k < 1 || k > 32 || n < 1) return MGEIG_EINVAL;
+    for (int j = 0; j < k; ++j)
+        if (!X[j]) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        blas_dot_host(c, k, X, y, (size_t)n, d);
+        return MGEIG_OK;
+    });
+}
+
+int mgeig_multi_axpy_dev(mgeig_ctx *ctx, int k, const void *const *X, const double *cf, void *y, long long n) {
+    if (!ctx || !X || !y || !cf || k < 1 || k > 32 || n < 1) return MGEIG_EINVAL;
+    for (int j = 0; j < k; ++j)
+        if (!X[j] || X[j] == y) return MGEIG_EINVAL;
+    return guarded(ctx, [&](Ctx &c) {
+        blas_axpy_host(c, k, X, cf, y, (size_t)n);
         return MGEIG_OK;
     });
 }

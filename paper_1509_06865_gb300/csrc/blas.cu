@@ -7,6 +7,7 @@
 // partial per block, and a second kernel adds the partials in a fixed order.
 // Inner products of up to 16 vectors against one vector share one read of that
 // vector (the Arnoldi / Gram-Schmidt steps of GMRES, FGMRES and Algorithm 1).
+#include "ds.cuh"
 #include "internal.h"
 
 namespace mgeig {
@@ -158,6 +159,121 @@ __global__ void finalize_kernel(const double2 *__restrict__ partial, size_t pstr
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 arrays, FP32 arithmetic: the double-float dot product and axpy.
+//
+// The FP64 pipe of this GPU issues about 1/64 of the FP32 rate, so the FP64
+// multidot / multi_axpy (4 FP64 FMAs per complex element and vector) are bound
+// by it at about a third of the memory rate.  These kernels read the same FP64
+// arrays and compute in FP32 with error-free transformations:
+//  * each double d becomes the unevaluated sum hi + lo of two floats by bit
+//    manipulation only (hi: sign, exponent and the leading 24 significant bits;
+//    lo: the next 23 bits), so |d - hi - lo| < 2^-46 |d| (Dekker's double-length
+//    representation, built here by truncation instead of rounding);
+//  * a product of two such numbers is hi*hi exactly as p + e (TwoProduct with
+//    one FMA) plus the cross terms hi*lo + lo*hi in FP32 (lo*lo < 2^-46 of the
+//    product is dropped);
+//  * p is added to the running high word by Knuth's TwoSum (exact: s + err), err,
+//    e and the cross terms to the low word.
+// This is the compensated dot product Dot2 of Ogita, Rump and Oishi (SIAM J.
+// Sci. Comput. 26, 2005) on double-float inputs: the result is as accurate as a
+// sum in 47-bit arithmetic, i.e. within a few 2^-46 sum|a_i b_i| of the exact
+// value (FP64 arithmetic: 2^-53 per operation).  The per-thread sums go to FP64
+// for the block and grid reductions.
+//
+// Range: elements with |d| < 2^-126 count as 0 and the low word is dropped below
+// 2^-80 (absolute errors below 2^-103 |d|-units); |d| >= 2^128 becomes +-inf (the
+// orthonormal vectors, Krylov vectors and iterates these kernels serve stay far
+// inside the range).  Every addition and multiplication below uses the _rn
+// intrinsics, which the compiler never contracts into an FMA.
+
+// (h, l) += (uh + ul)(vh + vl)
+__device__ __forceinline__ void ds_mac(float &h, float &l, float uh, float ul, float vh, float vl) {
+    const float p = __fmul_rn(uh, vh);
+    float e = fmaf(uh, vh, -p);
+    e = fmaf(uh, vl, e);
+    e = fmaf(ul, vh, e);
+    const float s = __fadd_rn(h, p);
+    const float bv = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+}
+
+constexpr int DS_CHUNK = 8;
+
+__global__ void __launch_bounds__(RED_THREADS) multidot_ds_kernel(PtrPack X, int k, const double2 *__restrict__ y,
+                                                                  size_t n, double2 *__restrict__ partial,
+                                                                  size_t pstride) {
+    float rh[DS_CHUNK], rl[DS_CHUNK], ih[DS_CHUNK], il[DS_CHUNK];
+#pragma unroll
+    for (int j = 0; j < DS_CHUNK; ++j) { rh[j] = rl[j] = ih[j] = il[j] = 0.0f; }
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 b = y[i];
+        float brh, brl, bih, bil;
+        ds_split(b.x, brh, brl);
+        ds_split(b.y, bih, bil);
+#pragma unroll
+        for (int j = 0; j < DS_CHUNK; ++j) {
+            if (j < k) {
+                const double2 a = static_cast<const double2 *>(X.p[j])[i];
+                float arh, arl, aih, ail;
+                ds_split(a.x, arh, arl);
+                ds_split(a.y, aih, ail);
+                // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+                ds_mac(rh[j], rl[j], arh, arl, brh, brl);
+                ds_mac(rh[j], rl[j], aih, ail, bih, bil);
+                ds_mac(ih[j], il[j], arh, arl, bih, bil);
+                ds_mac(ih[j], il[j], -aih, -ail, brh, brl);
+            }
+        }
+    }
+    double re[DS_CHUNK], im[DS_CHUNK];
+#pragma unroll
+    for (int j = 0; j < DS_CHUNK; ++j) {
+        re[j] = f2d_exact(rh[j]) + f2d_exact(rl[j]);
+        im[j] = f2d_exact(ih[j]) + f2d_exact(il[j]);
+    }
+    block_reduce_store<DS_CHUNK>(re, im, k, partial, pstride);
+}
+
+// y += sign * sum_j coef[j] X_j, y and X_j FP64, double-float arithmetic
+__global__ void __launch_bounds__(256) multi_axpy_ds_kernel(double2 *__restrict__ y, PtrPack X, int k,
+                                                            const double2 *__restrict__ coef, double sign, size_t n) {
+    float crh[DS_CHUNK], crl[DS_CHUNK], cih[DS_CHUNK], cil[DS_CHUNK];
+#pragma unroll
+    for (int j = 0; j < DS_CHUNK; ++j) {
+        if (j < k) {
+            const double2 t = coef[j];
+            ds_split(sign * t.x, crh[j], crl[j]);
+            ds_split(sign * t.y, cih[j], cil[j]);
+        } else {
+            crh[j] = crl[j] = cih[j] = cil[j] = 0.0f;
+        }
+    }
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 t = y[i];
+        float rh, rl, ih, il;
+        ds_split(t.x, rh, rl);
+        ds_split(t.y, ih, il);
+#pragma unroll
+        for (int j = 0; j < DS_CHUNK; ++j) {
+            if (j < k) {
+                const double2 a = static_cast<const double2 *>(X.p[j])[i];
+                float arh, arl, aih, ail;
+                ds_split(a.x, arh, arl);
+                ds_split(a.y, aih, ail);
+                // c a = (cr ar - ci ai) + i (cr ai + ci ar)
+                ds_mac(rh, rl, crh[j], crl[j], arh, arl);
+                ds_mac(rh, rl, -cih[j], -cil[j], aih, ail);
+                ds_mac(ih, il, crh[j], crl[j], aih, ail);
+                ds_mac(ih, il, cih[j], cil[j], arh, arl);
+            }
+        }
+        y[i] = make_double2(f2d_exact(rh) + f2d_exact(rl), f2d_exact(ih) + f2d_exact(il));
+    }
+}
+
 static double2 *partial_ptr(Ctx &c) { return c.red_partial.as<double2>(); }
 
 template <typename R>
@@ -165,13 +281,18 @@ void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n,
     const int nb = red_grid(n);
     const size_t pstride = RED_MAXBLOCKS;
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)(k + 1) * n * 2 * sizeof(R));
-    constexpr int C = Chunk<R>::n;
+    const bool ds = sizeof(R) == 8 && c.ds_blas();
+    const int C = ds ? DS_CHUNK : Chunk<R>::n;
     for (int j0 = 0; j0 < k; j0 += C) {
         PtrPack pk{};
         const int kk = k - j0 < C ? k - j0 : C;
         for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
-        multidot_kernel<R><<<nb, RED_THREADS, 0, c.stream>>>(pk, kk, y, n, partial_ptr(c) + (size_t)j0 * pstride, pstride,
-                                                             vec4_ok<R>(pk, kk, y, n));
+        if (ds)
+            multidot_ds_kernel<<<nb, RED_THREADS, 0, c.stream>>>(pk, kk, static_cast<const double2 *>(y), n,
+                                                                  partial_ptr(c) + (size_t)j0 * pstride, pstride);
+        else
+            multidot_kernel<R><<<nb, RED_THREADS, 0, c.stream>>>(pk, kk, y, n, partial_ptr(c) + (size_t)j0 * pstride,
+                                                                 pstride, vec4_ok<R>(pk, kk, y, n));
         MG_CHECK_LAUNCH();
     }
     finalize_kernel<<<k, 128, 0, c.stream>>>(partial_ptr(c), pstride, nb, reinterpret_cast<double2 *>(d_out));
@@ -254,14 +375,20 @@ static int ew_grid(size_t n) {
 template <typename R>
 void blas_multi_axpy(Ctx &c, void *y, const void *const *X, int k, const cpx<double> *d_coef, double sign, size_t n) {
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)(k + 2) * n * 2 * sizeof(R));
-    constexpr int C = Chunk<R>::n;
+    const bool ds = sizeof(R) == 8 && c.ds_blas();
+    const int C = ds ? DS_CHUNK : Chunk<R>::n;
     for (int j0 = 0; j0 < k; j0 += C) {
         PtrPack pk{};
         const int kk = k - j0 < C ? k - j0 : C;
         for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
-        const bool v4 = vec4_ok<R>(pk, kk, y, n);
-        multi_axpy_kernel<R><<<ew_grid(v4 ? n / 2 : n), 256, 0, c.stream>>>(
-            y, pk, kk, reinterpret_cast<const double2 *>(d_coef + j0), sign, n, v4);
+        if (ds) {
+            multi_axpy_ds_kernel<<<ew_grid(n), 256, 0, c.stream>>>(
+                static_cast<double2 *>(y), pk, kk, reinterpret_cast<const double2 *>(d_coef + j0), sign, n);
+        } else {
+            const bool v4 = vec4_ok<R>(pk, kk, y, n);
+            multi_axpy_kernel<R><<<ew_grid(v4 ? n / 2 : n), 256, 0, c.stream>>>(
+                y, pk, kk, reinterpret_cast<const double2 *>(d_coef + j0), sign, n, v4);
+        }
         MG_CHECK_LAUNCH();
     }
 }

@@ -666,6 +666,7 @@ CGPlan compute_plan(Ctx &c, int k) {
     MG_CUDA(cudaFuncGetAttributes(&fa, kern));
     const size_t elem = sizeof(cpx<R>);
     int G = std::max(1, std::min((n * TPR + CG_THREADS - 1) / CG_THREADS, dev_sms));
+    if (c.prm.coarse_blocks > 0) G = std::min(G, c.prm.coarse_blocks);
     p.rb = (n + G - 1) / G;
     p.G = (n + p.rb - 1) / p.rb;   // every block owns at least one row
     p.nslice = 2 * (p.m + 1) + 3;
@@ -690,9 +691,9 @@ CGPlan compute_plan(Ctx &c, int k) {
 template <typename R>
 CGPlan make_plan(Ctx &c, int k) {
     static std::mutex mu;
-    static std::map<std::array<int, 7>, CGPlan> cache;
-    const std::array<int, 7> key{c.device, c.nagg, c.prm.n_tv, std::min(c.prm.coarse_restart, CG_MAXM), k,
-                                 (int)sizeof(R), sizeof(R) == 4 ? c.prm.coarse_links : 0};
+    static std::map<std::array<int, 8>, CGPlan> cache;
+    const std::array<int, 8> key{c.device, c.nagg, c.prm.n_tv, std::min(c.prm.coarse_restart, CG_MAXM), k,
+                                 (int)sizeof(R), sizeof(R) == 4 ? c.prm.coarse_links : 0, c.prm.coarse_blocks};
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;

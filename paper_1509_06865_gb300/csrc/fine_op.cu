@@ -10,6 +10,7 @@
 // other sites also need), that is 672 bytes per site in FP32 (x 96, y 96,
 // two-row links 192, clover 288) and 1536 bytes in FP64 (x 192, y 192, full
 // links 576, clover 576).
+#include "ds.cuh"
 #include "internal.h"
 
 namespace mgeig {
@@ -40,6 +41,7 @@ __global__ void pack_gauge_kernel(int V, const double2 *__restrict__ in, double2
 
 void pack_gauge(Ctx &c, const double *dev_in) {
     const int V = c.g.V;
+    c.ds_fields_valid = false;
     TimeScope ts(c.timer, K_OTHER, 0);
     pack_gauge_kernel<<<grid_for(V, 128), 128, 0, c.stream>>>(V, reinterpret_cast<const double2 *>(dev_in),
                                                             c.U64.as<double2>(), c.U32.as<float4>());
@@ -203,6 +205,7 @@ __global__ void clover_build_kernel(Geom g, const double2 *__restrict__ u64, dou
 }
 
 void build_clover(Ctx &c) {
+    c.ds_fields_valid = false;
     double sig[2][6][4][2];
     host_sigma_blocks(sig);
     MG_CUDA(cudaMemcpyToSymbolAsync(c_sigma, sig, sizeof(sig), 0, cudaMemcpyHostToDevice, c.stream));
@@ -238,6 +241,7 @@ __global__ void pack_clover_kernel(int V, const double2 *__restrict__ in, double
 }
 
 void pack_clover(Ctx &c, const double *dev_in) {
+    c.ds_fields_valid = false;
     TimeScope ts(c.timer, K_OTHER, 0);
     pack_clover_kernel<<<grid_for(c.g.V, 128), 128, 0, c.stream>>>(c.g.V, reinterpret_cast<const double2 *>(dev_in),
                                                                    4.0 + c.prm.m0, c.clov64.as<double2>(),
@@ -290,6 +294,16 @@ struct InLoad<double, float> {
         Spinor<float>::load(base, V, s, t);
 #pragma unroll
         for (int k = 0; k < 12; ++k) v[k] = cpx<double>(t[k].re, t[k].im);
+    }
+};
+
+template <>
+struct InLoad<dsf, float> {
+    __device__ __forceinline__ static void load(const void *base, int V, int s, cpx<dsf> v[12]) {
+        cpx<float> t[12];
+        Spinor<float>::load(base, V, s, t);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = cpx<dsf>(dsf(t[k].re), dsf(t[k].im));
     }
 };
 
@@ -389,6 +403,49 @@ static void launch_fine(Ctx &c, int mode, double sigma, const void *x, void *y) 
     MG_CHECK_LAUNCH();
 }
 
+// double-float copies of the FP64 links and clover: (h, l) = (fl(d), fl(d - h))
+// for every double, a float2 at the double's index
+__global__ void ds_copy_kernel(size_t n, const double *__restrict__ in, float2 *__restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double d = in[i];
+        const float h = __double2float_rn(d);
+        out[i] = make_float2(h, __double2float_rn(d - (double)h));
+    }
+}
+
+static void ensure_ds_fields(Ctx &c) {
+    if (c.ds_fields_valid) return;
+    const size_t nu = (size_t)c.g.V * 4 * 9 * 2, nc = (size_t)c.g.V * 36 * 2;   // doubles
+    if (!c.Uds.p) c.Uds.alloc(nu * sizeof(float2));
+    if (!c.clovds.p) c.clovds.alloc(nc * sizeof(float2));
+    TimeScope ts(c.timer, K_OTHER, 0);
+    ds_copy_kernel<<<152 * 8, 256, 0, c.stream>>>(nu, c.U64.as<double>(), c.Uds.as<float2>());
+    MG_CHECK_LAUNCH();
+    ds_copy_kernel<<<152 * 8, 256, 0, c.stream>>>(nc, c.clov64.as<double>(), c.clovds.as<float2>());
+    MG_CHECK_LAUNCH();
+    c.ds_fields_valid = true;
+}
+
+// the FP64-output stencil in double-float arithmetic: FP64 (Rin = dsf) or FP32
+// (Rin = float) input, FP64 output, links and clover from the double-float copies
+template <typename Rin>
+static void launch_fine_ds(Ctx &c, int mode, double sigma, const void *x, void *y) {
+    ensure_ds_fields(c);
+    const int threads = 128;
+    const int blocks = grid_for(c.g.V, threads);
+    const void *U = c.Uds.p, *C = c.clovds.p;
+    const double spin = 12 * 2 * (sizeof(Rin) == 4 ? 4 : 8), spout = 12 * 2 * 8;
+    TimeScope ts(c.timer, K_STENCIL_F64, (spin + spout + 4 * 9 * 16 + 72 * 8) * c.g.V);
+    c.st.fine_applies += 1;
+    const dsf sg(sigma);
+    switch (mode) {
+        case MODE_D: wilson_clover_kernel<dsf, Rin, MODE_D><<<blocks, threads, 0, c.stream>>>(c.g, U, C, x, y, sg); break;
+        case MODE_DSIGMA: wilson_clover_kernel<dsf, Rin, MODE_DSIGMA><<<blocks, threads, 0, c.stream>>>(c.g, U, C, x, y, sg); break;
+        default: wilson_clover_kernel<dsf, Rin, MODE_QSIGMA><<<blocks, threads, 0, c.stream>>>(c.g, U, C, x, y, sg); break;
+    }
+    MG_CHECK_LAUNCH();
+}
+
 template <typename R>
 void apply_fine_nrhs(Ctx &c, int mode, double sigma, const void *x, void *y, int nrhs) {
     const int threads = 128;
@@ -414,15 +471,30 @@ void apply_fine_nrhs(Ctx &c, int mode, double sigma, const void *x, void *y, int
 template void apply_fine_nrhs<double>(Ctx &, int, double, const void *, void *, int);
 template void apply_fine_nrhs<float>(Ctx &, int, double, const void *, void *, int);
 
+// the solver's stencil: FP64 output in double-float arithmetic when the context
+// asks for it (mixed precision), else in R
 template <typename R>
 void apply_fine(Ctx &c, int mode, double sigma, const void *x, void *y) {
-    launch_fine<R, R>(c, mode, sigma, x, y);
+    if (sizeof(R) == 8 && c.ds_stencil()) launch_fine_ds<dsf>(c, mode, sigma, x, y);
+    else launch_fine<R, R>(c, mode, sigma, x, y);
 }
 template void apply_fine<double>(Ctx &, int, double, const void *, void *);
 template void apply_fine<float>(Ctx &, int, double, const void *, void *);
 
+// double-float arithmetic whatever the context asks (the ABI's double-float apply)
+void apply_fine_ds(Ctx &c, int mode, double sigma, const void *x, void *y, bool x_fp32) {
+    if (x_fp32) launch_fine_ds<float>(c, mode, sigma, x, y);
+    else launch_fine_ds<dsf>(c, mode, sigma, x, y);
+}
+
+// always FP64 arithmetic (the ABI's FP64 apply, the final eigen-residual check)
+void apply_fine_fp64(Ctx &c, int mode, double sigma, const void *x, void *y) {
+    launch_fine<double, double>(c, mode, sigma, x, y);
+}
+
 void apply_fine_f64_from_f32(Ctx &c, int mode, double sigma, const void *x32, void *y64) {
-    launch_fine<double, float>(c, mode, sigma, x32, y64);
+    if (c.ds_stencil()) launch_fine_ds<float>(c, mode, sigma, x32, y64);
+    else launch_fine<double, float>(c, mode, sigma, x32, y64);
 }
 
 // ---------------------------------------------------------------------------

@@ -113,6 +113,8 @@ template <typename R> void apply_fine(Ctx &c, int mode, double sigma, const void
 template <typename R> void apply_fine_nrhs(Ctx &c, int mode, double sigma, const void *x, void *y, int nrhs);
 // x in FP32 internal layout, y FP64: y = op(x) in FP64 arithmetic
 void apply_fine_f64_from_f32(Ctx &c, int mode, double sigma, const void *x32, void *y64);
+void apply_fine_fp64(Ctx &c, int mode, double sigma, const void *x, void *y);
+void apply_fine_ds(Ctx &c, int mode, double sigma, const void *x, void *y, bool x_fp32);
 void pack_spinor_f64(Ctx &c, const double *host_layout_dev, void *out, int n);
 void unpack_spinor_f64(Ctx &c, const void *in, double *host_layout_dev, int n);
 void convert_f64_to_f32(Ctx &c, const void *in64, void *out32, size_t ncomplex);
@@ -184,6 +186,8 @@ struct Ctx {
 
     // fine fields
     DevBuf U64, U32, clov64, clov32;
+    DevBuf Uds, clovds;          // double-float copies of U64, clov64 (float2 per double)
+    bool ds_fields_valid = false;
     DevBuf clov_user;         // a clover term loaded by mgeig_load_clover (host layout)
     bool clover_loaded = false;
     DevBuf staging;           // host-layout transfer buffer
@@ -210,6 +214,11 @@ struct Ctx {
     size_t fine_ncpx() const { return (size_t)g.V * 12; }
     size_t coarse_ncpx() const { return (size_t)nagg * 2 * prm.n_tv; }
     bool mixed() const { return prm.precision == MGEIG_MIXED; }
+    // FP64-storage BLAS and FP64-output stencil in double-float arithmetic
+    // (mixed precision only)
+    bool ds_blas() const { return prm.blas_ds != 0 && mixed() && !force_fp64; }
+    bool ds_stencil() const { return prm.stencil_ds != 0 && mixed() && !force_fp64; }
+    bool force_fp64 = false;     // set while a result is certified in FP64
     size_t level_bytes() const { return mixed() ? sizeof(float) : sizeof(double); }
 
     // host workspace counters
@@ -281,5 +290,7 @@ void lma_free(Ctx &c);
 void net_train(Ctx &c, int steps, int batch, double lr, uint64_t seed, double *losses);
 // FMA throughput (FLOP/s) of the library's own peak kernel, FP64 or FP32 (peak.cu)
 double fma_peak_flops(Ctx &c, int prec, int reps);
+void blas_dot_host(Ctx &c, int k, const void *const *X, const void *y, size_t n, double *out);
+void blas_axpy_host(Ctx &c, int k, const void *const *X, const double *coef, void *y, size_t n);
 
 }  // namespace mgeig

@@ -145,6 +145,25 @@ static cpx<double> *upload(Ctx &c, const std::vector<cpx<double>> &v) {
 
 static bool finite(cpx<double> z) { return std::isfinite(z.re) && std::isfinite(z.im); }
 
+// the Gram-Schmidt building blocks on caller-owned FP64 device vectors
+void blas_dot_host(Ctx &c, int k, const void *const *X, const void *y, size_t n, double *out) {
+    ensure_reduction(c, k);
+    blas_multidot<double>(c, X, k, y, n, dslot(c, H1));
+    fetch(c, H1 + k);
+    for (int j = 0; j < k; ++j) {
+        out[2 * j] = hslot(c, H1 + j)->re;
+        out[2 * j + 1] = hslot(c, H1 + j)->im;
+    }
+}
+
+void blas_axpy_host(Ctx &c, int k, const void *const *X, const double *coef, void *y, size_t n) {
+    ensure_reduction(c, k);
+    std::vector<cpx<double>> cv(k);
+    for (int j = 0; j < k; ++j) cv[j] = cpx<double>(coef[2 * j], coef[2 * j + 1]);
+    blas_multi_axpy<double>(c, y, X, k, upload(c, cv), 1.0, n);
+    sync(c);
+}
+
 // ---------------------------------------------------------------------------
 // workspace
 
@@ -1148,6 +1167,20 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
         }
     }
     c.st.sweeps = sweeps;
+    if (c.ds_blas() || c.ds_stencil()) {
+        // the reported pairs are certified in FP64: their Rayleigh quotients and
+        // residuals again with the FP64 stencil and FP64 inner products
+        struct Fp64 {
+            Ctx &c;
+            explicit Fp64(Ctx &cc) : c(cc) { c.force_fp64 = true; }
+            ~Fp64() { c.force_fp64 = false; }
+        } fp64{c};
+        for (int i = 0; i < (rr ? n_want : n_eig); ++i) {
+            auto le = rayleigh(c, M[i]);
+            lam[i] = le.first;
+            eps[i] = le.second;
+        }
+    }
     if (unconverged()) status = MGEIG_ENOCONV;
     // order by |lambda|, then lambda
     std::vector<int> ord(n_eig);

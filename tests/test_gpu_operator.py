@@ -76,6 +76,35 @@ def test_stencil_device_entry_point(case):
         assert norm_rel_err(got, want) < tol
 
 
+def test_stencil_double_float(case):
+    """The mixed solver's FP64-output stencil in double-float arithmetic (two
+    floats per value, links and clover from double-float copies): FP64 input,
+    and FP32 input (the outer FGMRES matvec of a preconditioned vector) against
+    the oracle applied to the same FP32-rounded input.  Double-float keeps about
+    47 bits, so the bound is 1e-12 where FP64 meets 1e-13 and FP32 1e-6."""
+    from paper_1509_06865_gb300 import OP_D, OP_Q, PREC_F32, PREC_F32_F64_DS, PREC_F64, PREC_F64_DS
+    ctx, op, c = case
+    V = ctx.V
+    x = synth.gaussian_vectors(c["dims"], 1, 9)
+    x32 = x.astype(np.complex64).astype(np.complex128)
+    px64, px32 = ctx.alloc_dev(V * 12 * 16), ctx.alloc_dev(V * 12 * 8)
+    py = ctx.alloc_dev(V * 12 * 16)
+    ctx.pack_spinors(x, px64, PREC_F64)
+    ctx.pack_spinors(x, px32, PREC_F32)
+    for opn, ref in ((OP_Q, op.Q_sigma), (OP_D, op.D_sigma)):
+        for sigma in (0.0, 0.0371):
+            ctx.apply_dev(px64, py, sigma, opn, PREC_F64_DS)
+            got = ctx.unpack_spinors(py, 1, PREC_F64)[0]
+            want = ref(x[0], sigma)
+            assert norm_rel_err(got, want) < 1e-12
+            assert rel_err(got, want) < 1e-12
+            ctx.apply_dev(px32, py, sigma, opn, PREC_F32_F64_DS)
+            got = ctx.unpack_spinors(py, 1, PREC_F64)[0]
+            want = ref(x32[0], sigma)
+            assert norm_rel_err(got, want) < 1e-12
+            assert rel_err(got, want) < 1e-12
+
+
 def _blocks(A12):
     """[..., 12, 12] site matrices -> [site][2][6][6] chirality blocks."""
     A = A12.reshape(-1, 12, 12)
