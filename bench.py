@@ -43,11 +43,10 @@ SINGLE_KERNEL_CLASSES = ("coarse_gmres", "stencil_f64", "stencil_f32", "sap_f32"
 # DRAM bytes (read + write) per launch from an ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where none was taken
 DRAM_BYTES_PER_LAUNCH = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:coarse_gmres -s 20 -c 3 on
-    # `python bench.py --profile-case eig16` (same 16^3x32 coarse grid): 66.0 MB read +
-    # 0.17 MB written per launch, whatever the number of GMRES steps (the coarse operator is read from DRAM once per
-    # solve and then served by L2)
-    "coarse_gmres": 66.17e6,
+    # ncu --set full -k regex:coarse_gmres -s 20 -c 2 on `python bench.py --profile-case eig16` (the same
+    # 16^3x32 coarse grid and the current kernel): 66.0 MB read + 0.46 MB written per launch, whatever the number
+    # of GMRES steps (the coarse operator is read from DRAM once per solve and then served by L2)
+    "coarse_gmres": 66.47e6,
 }
 
 
@@ -421,6 +420,42 @@ def north_star(args, flush, device):
     return out
 
 
+def config3_study(device=0, n_eig=50, setup_iters=30):
+    """The larger 32^3 x 64 workload: approximate modes straight from a setup of
+    `setup_iters` iterations (their Rayleigh quotients and eigen-residuals,
+    Sec. 3.3: about 1e-3 there), then the `n_eig` lowest pairs to 1e-10 by
+    Algorithm 1 (mixed precision, BF16 coarse links with per-link FP32 scale)."""
+    import numpy as np
+
+    import synth
+    from paper_1509_06865_gb300 import LINKS_BF16, MIXED, Context
+
+    cfg = workload("north_32x32x32x64")
+    dims = tuple(cfg["dims"])
+    ctx = Context(dims, device=device)
+    ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
+                   sap_block=cfg["sap_block"], precision=MIXED, coarse_links=LINKS_BF16, setup_iters=setup_iters)
+    ctx.load_gauge(synth.gauge_field(dims, cfg["eps"], cfg["seed"]))
+    t0 = time.perf_counter()
+    st0 = ctx.setup(cfg["seed"])
+    t_setup = time.perf_counter() - t0
+    appr = ctx.lma_prepare(cfg["n_tv"], None, 0.75)
+    order = np.argsort(np.abs(appr["lam"]))
+    t0 = time.perf_counter()
+    lam, _, res, st = ctx.eigensolve(n_eig, cfg["tol"], want_vectors=False)
+    t_eig = time.perf_counter() - t0
+    ctx.close()
+    out = dict(dims=list(dims), coarse_links="bf16", setup_iters=setup_iters, setup_s=t_setup,
+               approx_modes=dict(n=cfg["n_tv"], lam=[float(appr["lam"][i]) for i in order],
+                                 eps=[float(appr["eps"][i]) for i in order],
+                                 eps_median=float(np.median(appr["eps"])), n_kept_cutoff_0_75=int(appr["n_kept"])),
+               n_eig=n_eig, eig_s=t_eig, converged=st["converged"], max_resid=float(max(res)),
+               lambda_min=float(lam[0]), lambda_max=float(lam[-1]), sweeps=st["sweeps"], solves=st["solves"],
+               outer_iters=st["outer_iters"], coarse_iters=st["coarse_iters"])
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def small_field(flush, device):
     """The 4 lowest pairs of the 4^4 workload (mixed, to 1e-10), the field of the
     oracle's complete eigensolve in the CPU baseline: the like-for-like ratio of
@@ -628,12 +663,16 @@ def batch_study(device=0, nrhs=12, nsig=16):
     import synth
     from paper_1509_06865_gb300 import MIXED, Context, solve_batch
 
-    fields = [((8, 8, 8, 8), 1101), ((8, 8, 8, 8), 1102), ((16, 16, 16, 32), 1103), ((16, 16, 16, 32), 1104)]
+    # the six fields of uneven size (two each of 8^4, 12^3 x 24, 16^3 x 32); the
+    # 12^3 x 24 lattice takes SAP blocks of 3^4 (an even number of blocks per direction)
+    fields = [((8, 8, 8, 8), 1101), ((8, 8, 8, 8), 1102), ((12, 12, 12, 24), 1105), ((12, 12, 12, 24), 1106),
+              ((16, 16, 16, 32), 1103), ((16, 16, 16, 32), 1104)]
     ctxs, rhs = [], []
     for dims, seed in fields:
         ctx = Context(dims, device=device)
+        sap = (3, 3, 3, 3) if dims[0] == 12 else (4, 4, 4, 4)
         # m0 above the critical value of the 16^3x32 workload: min |lambda| > max sigma (no singular system)
-        ctx.set_params(m0=load_m0() + 0.06, csw=1.9, n_tv=20, precision=MIXED)
+        ctx.set_params(m0=load_m0() + 0.06, csw=1.9, n_tv=20, precision=MIXED, sap_block=sap)
         ctx.load_gauge(synth.gauge_field(dims, 0.2, seed))
         ctx.setup(seed)
         ctxs.append(ctx)
@@ -709,8 +748,10 @@ def main():
     ap.add_argument("--profile-case", choices=["eig16", "stencil32"])
     ap.add_argument("--neig-study", action="store_true",
                     help="time Algorithm 1 on the 16^3x32 field for 4..32 wanted pairs and with P from 12 / 6 modes")
+    ap.add_argument("--config3-study", action="store_true",
+                    help="32^3x64: approximate modes after a 30-iteration setup, then the 50 lowest pairs")
     ap.add_argument("--batch-study", action="store_true",
-                    help="16 shifts x 12 Z2 right-hand sides on four fields (8^4, 16^3x32) with mgeig_solve_batch")
+                    help="16 shifts x 12 Z2 right-hand sides on six fields (8^4, 12^3x24, 16^3x32) with mgeig_solve_batch")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
@@ -724,6 +765,9 @@ def main():
         return
     if args.batch_study:
         batch_study()
+        return
+    if args.config3_study:
+        config3_study()
         return
     if args.impl == "reference":
         run_reference(args)

@@ -175,6 +175,10 @@ typedef struct mgeig_params {
                              always FP64.  (On GB300 the double-float stencil is
                              slower than the FP64 one: its long dependent
                              TwoSum chains at 12 warps per SM are latency bound.) */
+    int blas_blocks;      /* thread blocks per SM of the BLAS-1 kernels (inner
+                             products, vector updates), at most 64; 0 = the
+                             measured defaults: 4 per SM for inner products and
+                             FP32 multi-vector updates, 16 for the others        */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */
@@ -490,21 +494,26 @@ int mgeig_net_loss_grads(mgeig_ctx *ctx, const double *x, const double *t, int b
  * rounding, result widened to FP64). */
 int mgeig_net_apply(mgeig_ctx *ctx, const double *r, double *e);
 
-/* Inner products d_j = <X_j, y> = sum_i conj(X_j[i]) y[i], j < k, of FP64
-   device vectors of n complex values (interleaved re, im, 16-byte aligned): the
-   projection coefficients of the Gram-Schmidt step of Algorithm 1 (Sec. 2.1)
-   and of the Arnoldi process of the outer FGMRES.  X: host array of k device
-   pointers (1 <= k <= 32); y: device pointer; d: host, 2k doubles (re, im).
-   The arithmetic follows the context's params: double-float when blas_ds = 1
-   and precision MGEIG_MIXED, else FP64.  Blocks until d is written.
-   Returns MGEIG_EINVAL for k out of range, n < 1 or a NULL pointer. */
-int mgeig_multidot_dev(mgeig_ctx *ctx, int k, const void *const *X, const void *y, long long n, double *d);
+/* Inner products d_j = <X_j, y> = sum_i conj(X_j[i]) y[i], j < k, of device
+   vectors of n complex values (interleaved re, im; FP64 for prec =
+   MGEIG_PREC_F64, FP32 for MGEIG_PREC_F32; 16-byte aligned): the projection
+   coefficients of the Gram-Schmidt step of Algorithm 1 (Sec. 2.1), of the
+   Arnoldi process of the outer FGMRES (FP64) and of the fine-grid deflation
+   (FP32).  X: host array of k device pointers (1 <= k <= 32); y: device
+   pointer; d: host, 2k doubles (re, im).  FP64 vectors: double-float arithmetic
+   when the context's blas_ds = 1 and precision MGEIG_MIXED, else FP64; FP32
+   vectors: FP32 products, per-thread FP32 sums, FP64 across threads.  Blocks
+   until d is written.  Returns MGEIG_EINVAL for prec or k out of range, n < 1
+   or a NULL pointer. */
+int mgeig_multidot_dev(mgeig_ctx *ctx, int prec, int k, const void *const *X, const void *y, long long n,
+                       double *d);
 
-/* y += sum_j c_j X_j, j < k (the update of the same Gram-Schmidt and Arnoldi
-   steps), for the FP64 device vectors of mgeig_multidot_dev; c: host, 2k
+/* y += sum_j c_j X_j, j < k (the update of the same Gram-Schmidt, Arnoldi and
+   deflation steps), for the device vectors of mgeig_multidot_dev; c: host, 2k
    doubles (re, im).  y must not be one of the X_j.  Same arithmetic rule and
    errors; returns when y is written. */
-int mgeig_multi_axpy_dev(mgeig_ctx *ctx, int k, const void *const *X, const double *c, void *y, long long n);
+int mgeig_multi_axpy_dev(mgeig_ctx *ctx, int prec, int k, const void *const *X, const double *c, void *y,
+                         long long n);
 
 /* FMA throughput of the device in FP64 (prec = MGEIG_PREC_F64) or FP32
  * (MGEIG_PREC_F32), in FLOP/s (2 per FMA), measured with the library's own

@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("fine_deflate", C.c_int), ("fine_deflate_radius", C.c_double),
         ("adaptive_tol", C.c_int), ("ritz_start", C.c_int), ("coarse_links", C.c_int), ("p_modes", C.c_int),
         ("barrier_timeout", C.c_double), ("coarse_blocks", C.c_int), ("blas_ds", C.c_int),
-        ("stencil_ds", C.c_int),
+        ("stencil_ds", C.c_int), ("blas_blocks", C.c_int),
     ]
 
 
@@ -109,8 +109,8 @@ def load():
         "mgeig_get_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
         "mgeig_mg_cycle_dev_noalloc": (I, [P, D, P, P]),
         "mgeig_fma_peak": (I, [P, I, I, C.POINTER(D)]),
-        "mgeig_multidot_dev": (I, [P, I, P, P, C.c_longlong, P]),
-        "mgeig_multi_axpy_dev": (I, [P, I, P, P, P, C.c_longlong]),
+        "mgeig_multidot_dev": (I, [P, I, I, P, P, C.c_longlong, P]),
+        "mgeig_multi_axpy_dev": (I, [P, I, I, P, P, P, C.c_longlong]),
         "mgeig_lma_prepare": (I, [P, I, P, D, P, P, P, P, P, P, P]),
         "mgeig_lma_apply": (I, [P, I, P, P]),
         "mgeig_lma_loop_high": (I, [P, I, C.c_uint64, D, P, C.POINTER(Stats)]),
@@ -461,20 +461,22 @@ class Context:
         self._check("mgeig_fma_peak", self.lib.mgeig_fma_peak(self._h, prec, int(reps), C.byref(f)))
         return f.value
 
-    def multidot_dev(self, X_ptrs, y_ptr: int, n: int) -> np.ndarray:
-        """<X_j, y> for FP64 device vectors of n complex values."""
+    def multidot_dev(self, X_ptrs, y_ptr: int, n: int, prec=PREC_F64) -> np.ndarray:
+        """<X_j, y> for device vectors of n complex values (FP64 or FP32)."""
         k = len(X_ptrs)
         arr = (C.c_void_p * k)(*X_ptrs)
         d = np.zeros(2 * k)
-        self._check("mgeig_multidot_dev", self.lib.mgeig_multidot_dev(self._h, k, arr, C.c_void_p(y_ptr), n, _ptr(d)))
+        self._check("mgeig_multidot_dev",
+                    self.lib.mgeig_multidot_dev(self._h, prec, k, arr, C.c_void_p(y_ptr), n, _ptr(d)))
         return d[0::2] + 1j * d[1::2]
 
-    def multi_axpy_dev(self, X_ptrs, coef, y_ptr: int, n: int):
-        """y += sum_j coef[j] X_j for FP64 device vectors of n complex values."""
+    def multi_axpy_dev(self, X_ptrs, coef, y_ptr: int, n: int, prec=PREC_F64):
+        """y += sum_j coef[j] X_j for device vectors of n complex values (FP64 or FP32)."""
         k = len(X_ptrs)
         arr = (C.c_void_p * k)(*X_ptrs)
         cf = np.ascontiguousarray(np.stack([np.real(coef), np.imag(coef)], axis=1).ravel(), dtype=np.float64)
-        self._check("mgeig_multi_axpy_dev", self.lib.mgeig_multi_axpy_dev(self._h, k, arr, _ptr(cf), C.c_void_p(y_ptr), n))
+        self._check("mgeig_multi_axpy_dev",
+                    self.lib.mgeig_multi_axpy_dev(self._h, prec, k, arr, _ptr(cf), C.c_void_p(y_ptr), n))
 
     def launch_count(self) -> int:
         n = C.c_longlong()

@@ -63,6 +63,7 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (p.coarse_blocks < 0) return MGEIG_EINVAL;
     if (p.blas_ds != 0 && p.blas_ds != 1) return MGEIG_EINVAL;
     if (p.stencil_ds != 0 && p.stencil_ds != 1) return MGEIG_EINVAL;
+    if (p.blas_blocks < 0 || p.blas_blocks > 64) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES && p.smoother != MGEIG_LEARNED) return MGEIG_EINVAL;
@@ -134,6 +135,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->coarse_blocks = 0;
     p->blas_ds = 1;
     p->stencil_ds = 0;
+    p->blas_blocks = 0;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
@@ -161,6 +163,7 @@ int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
     mgeig_default_params(&c.prm);
     int rc = guarded(ctx, [&](Ctx &c) {
         MG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        MG_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device));
         c.timer.stream = c.stream;
         c.U64.alloc((size_t)V * 4 * 9 * 16);
         c.U32.alloc((size_t)V * 4 * 3 * 16);
@@ -840,22 +843,26 @@ int mgeig_net_apply(mgeig_ctx *ctx, const double *r, double *e) {
     });
 }
 
-int mgeig_multidot_dev(mgeig_ctx *ctx, int k, const void *const *X, const void *y, long long n, double *d) {
+int mgeig_multidot_dev(mgeig_ctx *ctx, int prec, int k, const void *const *X, const void *y, long long n,
+                       double *d) {
     if (!ctx || !X || !y || !d || k < 1 || k > 32 || n < 1) return MGEIG_EINVAL;
+    if (prec != MGEIG_PREC_F64 && prec != MGEIG_PREC_F32) return MGEIG_EINVAL;
     for (int j = 0; j < k; ++j)
         if (!X[j]) return MGEIG_EINVAL;
     return guarded(ctx, [&](Ctx &c) {
-        blas_dot_host(c, k, X, y, (size_t)n, d);
+        blas_dot_host(c, prec == MGEIG_PREC_F32, k, X, y, (size_t)n, d);
         return MGEIG_OK;
     });
 }
 
-int mgeig_multi_axpy_dev(mgeig_ctx *ctx, int k, const void *const *X, const double *cf, void *y, long long n) {
+int mgeig_multi_axpy_dev(mgeig_ctx *ctx, int prec, int k, const void *const *X, const double *cf, void *y,
+                         long long n) {
     if (!ctx || !X || !y || !cf || k < 1 || k > 32 || n < 1) return MGEIG_EINVAL;
+    if (prec != MGEIG_PREC_F64 && prec != MGEIG_PREC_F32) return MGEIG_EINVAL;
     for (int j = 0; j < k; ++j)
         if (!X[j] || X[j] == y) return MGEIG_EINVAL;
     return guarded(ctx, [&](Ctx &c) {
-        blas_axpy_host(c, k, X, cf, y, (size_t)n);
+        blas_axpy_host(c, prec == MGEIG_PREC_F32, k, X, cf, y, (size_t)n);
         return MGEIG_OK;
     });
 }

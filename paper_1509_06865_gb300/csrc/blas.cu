@@ -7,6 +7,8 @@
 // partial per block, and a second kernel adds the partials in a fixed order.
 // Inner products of up to 16 vectors against one vector share one read of that
 // vector (the Arnoldi / Gram-Schmidt steps of GMRES, FGMRES and Algorithm 1).
+#include <algorithm>
+
 #include "ds.cuh"
 #include "internal.h"
 
@@ -36,8 +38,14 @@ static bool vec4_ok(const PtrPack &pk, int k, const void *y, size_t n) {
     return true;
 }
 
-static int red_grid(size_t n) {
+// reduction grids: one block per 4 * 256 elements, at most 4 blocks per SM (or
+// blas_blocks per SM when the context sets it) and 1024 in all.  Measured on
+// GB300 (16 FP32 or 8 double-float vectors per launch): 4 per SM beat 1024
+// blocks by 1.1-1.35x at 16^3 x 32 and 32^3 x 64 (fewer block epilogues and
+// partial sums)
+static int red_grid(const Ctx &c, size_t n) {
     size_t b = (n + RED_THREADS * 4 - 1) / (RED_THREADS * 4);
+    b = std::min<size_t>(b, (size_t)c.sms * (c.prm.blas_blocks > 0 ? c.prm.blas_blocks : 4));
     if (b < 1) b = 1;
     if (b > RED_MAXBLOCKS) b = RED_MAXBLOCKS;
     return (int)b;
@@ -278,7 +286,7 @@ static double2 *partial_ptr(Ctx &c) { return c.red_partial.as<double2>(); }
 
 template <typename R>
 void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n, cpx<double> *d_out) {
-    const int nb = red_grid(n);
+    const int nb = red_grid(c, n);
     const size_t pstride = RED_MAXBLOCKS;
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)(k + 1) * n * 2 * sizeof(R));
     const bool ds = sizeof(R) == 8 && c.ds_blas();
@@ -301,7 +309,7 @@ void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n,
 
 template <typename R>
 void blas_norm2(Ctx &c, const void *x, size_t n, cpx<double> *d_out) {
-    const int nb = red_grid(n);
+    const int nb = red_grid(c, n);
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)n * 2 * sizeof(R));
     norm2_kernel<R><<<nb, RED_THREADS, 0, c.stream>>>(x, n, partial_ptr(c));
     MG_CHECK_LAUNCH();
@@ -310,7 +318,7 @@ void blas_norm2(Ctx &c, const void *x, size_t n, cpx<double> *d_out) {
 }
 
 void blas_resid_norm2(Ctx &c, const void *qv, const void *v, const cpx<double> *d_lambda, size_t n, cpx<double> *d_out) {
-    const int nb = red_grid(n);
+    const int nb = red_grid(c, n);
     TimeScope ts(c.timer, K_BLAS_F64, (double)n * 32);
     resid_norm2_kernel<<<nb, RED_THREADS, 0, c.stream>>>(static_cast<const double2 *>(qv), static_cast<const double2 *>(v),
                                                          reinterpret_cast<const double2 *>(d_lambda), n, partial_ptr(c));
@@ -366,9 +374,13 @@ __global__ void multi_axpy_kernel(void *__restrict__ yv, PtrPack X, int k, const
     }
 }
 
-static int ew_grid(size_t n) {
+// element-wise grids: one thread per element up to per_sm blocks per SM (or
+// blas_blocks per SM when the context sets it).  The FP32 multi-vector update
+// runs best at 4 per SM (1.5x over 16 at 16^3 x 32), the double-float one,
+// bound by its FP32 arithmetic, at 16
+static int ew_grid(const Ctx &c, size_t n, int per_sm = 16) {
     size_t b = (n + 255) / 256;
-    const size_t cap = 152 * 16;
+    const size_t cap = (size_t)c.sms * (c.prm.blas_blocks > 0 ? c.prm.blas_blocks : per_sm);
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
@@ -382,11 +394,11 @@ void blas_multi_axpy(Ctx &c, void *y, const void *const *X, int k, const cpx<dou
         const int kk = k - j0 < C ? k - j0 : C;
         for (int j = 0; j < kk; ++j) pk.p[j] = X[j0 + j];
         if (ds) {
-            multi_axpy_ds_kernel<<<ew_grid(n), 256, 0, c.stream>>>(
+            multi_axpy_ds_kernel<<<ew_grid(c, n), 256, 0, c.stream>>>(
                 static_cast<double2 *>(y), pk, kk, reinterpret_cast<const double2 *>(d_coef + j0), sign, n);
         } else {
             const bool v4 = vec4_ok<R>(pk, kk, y, n);
-            multi_axpy_kernel<R><<<ew_grid(v4 ? n / 2 : n), 256, 0, c.stream>>>(
+            multi_axpy_kernel<R><<<ew_grid(c, v4 ? n / 2 : n, sizeof(R) == 4 ? 4 : 16), 256, 0, c.stream>>>(
                 y, pk, kk, reinterpret_cast<const double2 *>(d_coef + j0), sign, n, v4);
         }
         MG_CHECK_LAUNCH();
@@ -424,14 +436,14 @@ __global__ void scale_kernel(double ar, double ai, void *__restrict__ xv, size_t
 template <typename R>
 void blas_axpy(Ctx &c, cpx<double> a, const void *x, void *y, size_t n) {
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, 3.0 * n * 2 * sizeof(R));
-    axpy_kernel<R><<<ew_grid(n), 256, 0, c.stream>>>(a.re, a.im, x, y, n);
+    axpy_kernel<R><<<ew_grid(c, n), 256, 0, c.stream>>>(a.re, a.im, x, y, n);
     MG_CHECK_LAUNCH();
 }
 
 template <typename R>
 void blas_scale(Ctx &c, cpx<double> a, void *x, size_t n) {
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, 2.0 * n * 2 * sizeof(R));
-    scale_kernel<R><<<ew_grid(n), 256, 0, c.stream>>>(a.re, a.im, x, n);
+    scale_kernel<R><<<ew_grid(c, n), 256, 0, c.stream>>>(a.re, a.im, x, n);
     MG_CHECK_LAUNCH();
 }
 

@@ -52,6 +52,8 @@
 namespace mgeig {
 
 constexpr int CG_THREADS = 1024;
+constexpr int CG_GATHER = 8;                      // partial sums per lane: up to 256 blocks
+constexpr int CG_NBR_SITES = 64;                  // coarse sites of a block's staged neighbour table
 constexpr int CG_MAXM = COARSE_PERSISTENT_MAXM;   // restart length limit
 constexpr int CG_MAXK = 24;                       // deflation vectors (= max N_tv)
 // partial-sum regions of consecutive reductions never overlap
@@ -141,8 +143,16 @@ __device__ __forceinline__ cpx<double> ldcg(const cpx<double> *p) {
 // hop blocks, and the group reduces with shuffles.
 constexpr int TPR = 8;
 
+// The neighbour aggregate of hop d of site `site`: from the block's staged table
+// (sites s0 .. s0 + CG_NBR_SITES - 1) when there is one, else from global memory.
 template <typename R>
-__device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1) {
+__device__ __forceinline__ int hop_nbr(const CGArgs<R> &a, const int *snb, int s0, int d, int site) {
+    return snb ? snb[d * CG_NBR_SITES + site - s0] : __ldg(a.nbr + (size_t)d * a.nagg + site);
+}
+
+template <typename R>
+__device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1,
+                                        const int *snb, int s0) {
     const int n2 = 2 * a.ntv;
     const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
     for (int tb = r0; tb < r1; tb += ngrp) {
@@ -155,7 +165,7 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
                 // loaded before they are used, so their L2 latencies overlap
                 constexpr int U = (2 * CG_MAXK + TPR - 1) / TPR;
                 for (int d = 0; d < 9; ++d) {
-                    const int nb = __ldg(a.nbr + (size_t)d * a.nagg + site);
+                    const int nb = hop_nbr(a, snb, s0, d, site);
                     const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
                     const cpx<R> *xb = v + (size_t)nb * n2;
                     cpx<R> bv[U], xv[U];
@@ -171,7 +181,7 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
             } else {
 #pragma unroll 3
                 for (int d = 0; d < 9; ++d) {
-                    const int nb = __ldg(a.nbr + (size_t)d * a.nagg + site);
+                    const int nb = hop_nbr(a, snb, s0, d, site);
                     const cpx<R> *blk = a.Dc + ((size_t)d * a.nagg + site) * n2 * n2 + row;
                     const cpx<R> *xb = v + (size_t)nb * n2;
                     int j = q;
@@ -200,7 +210,7 @@ __device__ __forceinline__ void qmatvec(const CGArgs<R> &a, const cpx<R> *v, R s
 // hop block's sum is multiplied by the block's scale.
 template <typename H>
 __device__ __forceinline__ void qmatvec16(const CGArgs<float> &a, const cpx<float> *v, float s, cpx<float> *out,
-                                          int r0, int r1) {
+                                          int r0, int r1, const int *snb, int s0) {
     using HP = typename H16<H>::P;
     const int n2 = 2 * a.ntv, np = a.ntv;
     const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
@@ -213,7 +223,7 @@ __device__ __forceinline__ void qmatvec16(const CGArgs<float> &a, const cpx<floa
             const int site = t / n2, row = t % n2;
             for (int d = 0; d < 9; ++d) {
                 const size_t blk = (size_t)d * a.nagg + site;
-                const int nb = __ldg(a.nbr + blk);
+                const int nb = hop_nbr(a, snb, s0, d, site);
                 const HP *pr = reinterpret_cast<const HP *>(L + blk * 2 * n2 * n2 + (size_t)row * n2);
                 const HP *pi = pr + (size_t)n2 * n2 / 2;
                 const float4 *xb = reinterpret_cast<const float4 *>(v + (size_t)nb * n2);
@@ -255,10 +265,11 @@ __device__ __forceinline__ void qmatvec16(const CGArgs<float> &a, const cpx<floa
 
 // the product of the kernel's link format LK (0: level precision, 1: BF16, 2: FP16)
 template <typename R, int LK>
-__device__ __forceinline__ void matvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1) {
-    if constexpr (LK == 0) qmatvec<R>(a, v, s, out, r0, r1);
-    else if constexpr (LK == 1) qmatvec16<__nv_bfloat16>(a, v, s, out, r0, r1);
-    else qmatvec16<__half>(a, v, s, out, r0, r1);
+__device__ __forceinline__ void matvec(const CGArgs<R> &a, const cpx<R> *v, R s, cpx<R> *out, int r0, int r1,
+                                       const int *snb, int s0) {
+    if constexpr (LK == 0) qmatvec<R>(a, v, s, out, r0, r1, snb, s0);
+    else if constexpr (LK == 1) qmatvec16<__nv_bfloat16>(a, v, s, out, r0, r1, snb, s0);
+    else qmatvec16<__half>(a, v, s, out, r0, r1, snb, s0);
 }
 
 // Scalars (partial sums, Hessenberg matrix, Givens rotations, E^-1) are kept in
@@ -307,6 +318,17 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     auto AWv = [&](int l) -> const cpx<R> * { return Dl ? Dl + (size_t)(k + l) * rb : a.AW + (size_t)l * a.n + r0; };
     auto g5 = [&](int i, cpx<R> v) { return ((r0 + i) % n2) >= a.ntv ? -v : v; };
 
+    // the neighbour table of the block's coarse sites, staged once (the matvec's
+    // block loads then wait on one L2 round trip per hop instead of two)
+    __shared__ int snb[9 * CG_NBR_SITES];
+    const int s0 = nr > 0 ? r0 / n2 : 0;
+    const int nsites = nr > 0 ? (r1 - 1) / n2 - s0 + 1 : 0;
+    const int *snb_p = nsites <= CG_NBR_SITES ? snb : nullptr;
+    if (snb_p)
+        for (int e = threadIdx.x; e < 9 * nsites; e += blockDim.x) {
+            const int d = e / nsites, sl = e % nsites;
+            snb[d * CG_NBR_SITES + sl] = __ldg(a.nbr + (size_t)d * a.nagg + s0 + sl);
+        }
     for (int i = threadIdx.x; i < k * k; i += blockDim.x) Ei[i] = P2((R)a.Einv[i].x, (R)a.Einv[i].y);
     if (threadIdx.x < CG_MAXK) { tc[threadIdx.x] = P2(0, 0); t0[threadIdx.x] = P2(0, 0); }
     if (Dl)
@@ -358,11 +380,18 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) mypart[off + i] = wpart[i];
         if (!grid_sync(a.st, G, a.timeout)) return false;
         for (int i = wp; i < cnt; i += nw) {
-            R sr = 0, si = 0;
-            for (unsigned int q = lane; q < G; q += 32) {
-                P p = __ldcg(a.partial + (size_t)q * CG_SLOTS + off + i);
-                sr += p.x; si += p.y;
+            // all of a lane's partials are loaded before they are added (G <= 32 *
+            // CG_GATHER), so their L2 latencies overlap; the order of the sums is
+            // the same in every block
+            P pv[CG_GATHER];
+#pragma unroll
+            for (int u = 0; u < CG_GATHER; ++u) {
+                const unsigned int q = lane + 32u * u;
+                pv[u] = q < G ? __ldcg(a.partial + (size_t)q * CG_SLOTS + off + i) : P{0, 0};
             }
+            R sr = 0, si = 0;
+#pragma unroll
+            for (int u = 0; u < CG_GATHER; ++u) { sr += pv[u].x; si += pv[u].y; }
             for (int o = 16; o > 0; o >>= 1) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 si += __shfl_xor_sync(0xffffffffu, si, o);
@@ -448,7 +477,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         if (have_x) {
             publish(xs);
             if (!grid_sync(a.st, G, a.timeout)) return;       // x complete everywhere
-            matvec<R, LK>(a, a.pub, R(1), v0, r0, r1);
+            matvec<R, LK>(a, a.pub, R(1), v0, r0, r1, snb_p, s0);
             __syncthreads();
             if (k > 0) {
                 if (!deflation_coeffs(v0)) return;             // its barrier also ends the reads of pub
@@ -481,7 +510,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             const cpx<R> *vj = Vv(j);
             // U_j = A s_j V_j: the matvec of pub (= V_j before its second pass),
             // corrected by the second-pass coefficients of the last step
-            matvec<R, LK>(a, a.pub, (R)scale[j], uj, r0, r1);
+            matvec<R, LK>(a, a.pub, (R)scale[j], uj, r0, r1, snb_p, s0);
             __syncthreads();
             if (j > 0)
                 combine(j, Uv, [&](int i) { return cpx<R>((R)(h2s[i].x * scale[j]), (R)(h2s[i].y * scale[j])); },
@@ -615,7 +644,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
     if (k > 0) {
         publish(xs);
         if (!grid_sync(a.st, G, a.timeout)) return;
-        matvec<R, LK>(a, a.pub, R(1), ws, r0, r1);
+        matvec<R, LK>(a, a.pub, R(1), ws, r0, r1, snb_p, s0);
         __syncthreads();
         if (!deflation_coeffs(ws)) return;
         combine(k, Wv, [&](int i) { return cpx<R>((R)(t0[i].x - tc[i].x), (R)(t0[i].y - tc[i].y)); }, xs,
@@ -667,6 +696,7 @@ CGPlan compute_plan(Ctx &c, int k) {
     const size_t elem = sizeof(cpx<R>);
     int G = std::max(1, std::min((n * TPR + CG_THREADS - 1) / CG_THREADS, dev_sms));
     if (c.prm.coarse_blocks > 0) G = std::min(G, c.prm.coarse_blocks);
+    G = std::min(G, 32 * CG_GATHER);
     p.rb = (n + G - 1) / G;
     p.G = (n + p.rb - 1) / p.rb;   // every block owns at least one row
     p.nslice = 2 * (p.m + 1) + 3;

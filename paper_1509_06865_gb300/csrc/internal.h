@@ -176,6 +176,7 @@ struct Ctx {
     int dims[4];
     Geom g;
     int device = 0;
+    int sms = 152;               // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     mgeig_params prm;
     bool have_gauge = false;
@@ -290,7 +291,7 @@ void lma_free(Ctx &c);
 void net_train(Ctx &c, int steps, int batch, double lr, uint64_t seed, double *losses);
 // FMA throughput (FLOP/s) of the library's own peak kernel, FP64 or FP32 (peak.cu)
 double fma_peak_flops(Ctx &c, int prec, int reps);
-void blas_dot_host(Ctx &c, int k, const void *const *X, const void *y, size_t n, double *out);
-void blas_axpy_host(Ctx &c, int k, const void *const *X, const double *coef, void *y, size_t n);
+void blas_dot_host(Ctx &c, bool f32, int k, const void *const *X, const void *y, size_t n, double *out);
+void blas_axpy_host(Ctx &c, bool f32, int k, const void *const *X, const double *coef, void *y, size_t n);
 
 }  // namespace mgeig

@@ -146,9 +146,10 @@ static cpx<double> *upload(Ctx &c, const std::vector<cpx<double>> &v) {
 static bool finite(cpx<double> z) { return std::isfinite(z.re) && std::isfinite(z.im); }
 
 // the Gram-Schmidt building blocks on caller-owned FP64 device vectors
-void blas_dot_host(Ctx &c, int k, const void *const *X, const void *y, size_t n, double *out) {
+void blas_dot_host(Ctx &c, bool f32, int k, const void *const *X, const void *y, size_t n, double *out) {
     ensure_reduction(c, k);
-    blas_multidot<double>(c, X, k, y, n, dslot(c, H1));
+    if (f32) blas_multidot<float>(c, X, k, y, n, dslot(c, H1));
+    else blas_multidot<double>(c, X, k, y, n, dslot(c, H1));
     fetch(c, H1 + k);
     for (int j = 0; j < k; ++j) {
         out[2 * j] = hslot(c, H1 + j)->re;
@@ -156,11 +157,12 @@ void blas_dot_host(Ctx &c, int k, const void *const *X, const void *y, size_t n,
     }
 }
 
-void blas_axpy_host(Ctx &c, int k, const void *const *X, const double *coef, void *y, size_t n) {
+void blas_axpy_host(Ctx &c, bool f32, int k, const void *const *X, const double *coef, void *y, size_t n) {
     ensure_reduction(c, k);
     std::vector<cpx<double>> cv(k);
     for (int j = 0; j < k; ++j) cv[j] = cpx<double>(coef[2 * j], coef[2 * j + 1]);
-    blas_multi_axpy<double>(c, y, X, k, upload(c, cv), 1.0, n);
+    if (f32) blas_multi_axpy<float>(c, y, X, k, upload(c, cv), 1.0, n);
+    else blas_multi_axpy<double>(c, y, X, k, upload(c, cv), 1.0, n);
     sync(c);
 }
 
@@ -703,25 +705,28 @@ void setup(Ctx &c, uint64_t seed) {
 // so span(Z) is solved exactly (Galerkin) and the two-grid method B only sees
 // the deflated residual.  The iteration still solves (Q - sigma) x = v.
 
-// Q z_i, its level-precision copies and row/column i of Z^dag Z, Z^dag Q Z
-static void fdefl_update(Ctx &c, const std::vector<void *> &M, int i) {
+// Q z_i, its level-precision copies and row/column i of Z^dag Z, Z^dag Q Z: the
+// entries j < upto (all of them after z_i changed; j <= i when every row is
+// rebuilt in order, the Hermitian matrices giving the rest)
+static void fdefl_update(Ctx &c, const std::vector<void *> &M, int i, int upto = -1) {
     Ctx::Work &w = *c.work;
     const size_t N = c.fine_ncpx();
-    const int k = w.fd_n;
+    const int k = upto < 0 ? w.fd_n : upto;
     apply_fine<double>(c, MODE_QSIGMA, 0.0, M[i], w.QZ64[i]);
     std::vector<const void *> X(M.begin(), M.begin() + k);
     blas_multidot<double>(c, X.data(), k, M[i], N, dslot(c, H1));
     blas_multidot<double>(c, X.data(), k, w.QZ64[i], N, dslot(c, H2));
     fetch(c, H2 + k);
+    const int kk = w.fd_n;   // the matrices' leading dimension
     for (int j = 0; j < k; ++j) {
         const cpx<double> g = *hslot(c, H1 + j), h = *hslot(c, H2 + j);   // <z_j, z_i>, <z_j, Q z_i>
-        w.Gz[(size_t)j * k + i] = g;
-        w.Gz[(size_t)i * k + j] = conj(g);
-        w.Hz[(size_t)j * k + i] = h;
-        w.Hz[(size_t)i * k + j] = conj(h);   // Q is Hermitian
+        w.Gz[(size_t)j * kk + i] = g;
+        w.Gz[(size_t)i * kk + j] = conj(g);
+        w.Hz[(size_t)j * kk + i] = h;
+        w.Hz[(size_t)i * kk + j] = conj(h);   // Q is Hermitian
     }
-    w.Gz[(size_t)i * k + i] = cpx<double>(w.Gz[(size_t)i * k + i].re);
-    w.Hz[(size_t)i * k + i] = cpx<double>(w.Hz[(size_t)i * k + i].re);
+    w.Gz[(size_t)i * kk + i] = cpx<double>(w.Gz[(size_t)i * kk + i].re);
+    w.Hz[(size_t)i * kk + i] = cpx<double>(w.Hz[(size_t)i * kk + i].re);
     if (c.mixed()) {
         convert_f64_to_f32(c, M[i], w.fdZ[i], N);
         convert_f64_to_f32(c, w.QZ64[i], w.fdQZ[i], N);
@@ -732,7 +737,7 @@ static void fdefl_update(Ctx &c, const std::vector<void *> &M, int i) {
 }
 
 static void fdefl_all(Ctx &c, const std::vector<void *> &M) {
-    for (int i = 0; i < c.work->fd_n; ++i) fdefl_update(c, M, i);
+    for (int i = 0; i < c.work->fd_n; ++i) fdefl_update(c, M, i, i + 1);
 }
 
 static void fdefl_begin(Ctx &c, const std::vector<void *> &M, int k) {

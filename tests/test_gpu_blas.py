@@ -65,6 +65,53 @@ def test_multidot(blas_ds, precision, name, n, k):
     ctx.close()
 
 
+BOUND32 = 2.0 ** -18   # FP32 products and per-thread FP32 sums of at most a few hundred terms
+
+
+@pytest.mark.parametrize("n", [1, 255, 1000003])
+@pytest.mark.parametrize("k", [1, 16, 21])
+def test_multidot_fp32(n, k):
+    """The FP32 vectors of the fine-grid deflation (level precision)."""
+    import torch
+    from paper_1509_06865_gb300 import PREC_F32
+    rng = np.random.default_rng(77 * k + n % 1000)
+    X = random_vectors(rng, k, n).astype(np.complex64)
+    y = random_vectors(rng, 1, n)[0].astype(np.complex64)
+    ctx = ctx_for(1, 1)
+    Xd = [torch.from_numpy(x).to("cuda:0") for x in X]
+    yd = torch.from_numpy(y).to("cuda:0")
+    torch.cuda.synchronize()
+    d = ctx.multidot_dev([t.data_ptr() for t in Xd], yd.data_ptr(), n, prec=PREC_F32)
+    X64, y64 = X.astype(np.complex128), y.astype(np.complex128)
+    want = np.array([np.vdot(x, y64) for x in X64])
+    scale = np.abs(X64) @ np.abs(y64)
+    assert np.all(np.abs(d - want) <= BOUND32 * scale)
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [1, 1000003])
+@pytest.mark.parametrize("k", [1, 16, 19])
+def test_multi_axpy_fp32(n, k):
+    import torch
+    from paper_1509_06865_gb300 import PREC_F32
+    rng = np.random.default_rng(91 * k + n % 1000)
+    X = random_vectors(rng, k, n).astype(np.complex64)
+    y = random_vectors(rng, 1, n)[0].astype(np.complex64)
+    c = rng.standard_normal(k) + 1j * rng.standard_normal(k)
+    ctx = ctx_for(1, 1)
+    Xd = [torch.from_numpy(x).to("cuda:0") for x in X]
+    yd = torch.from_numpy(y.copy()).to("cuda:0")
+    torch.cuda.synchronize()
+    ctx.multi_axpy_dev([t.data_ptr() for t in Xd], c, yd.data_ptr(), n, prec=PREC_F32)
+    got = yd.cpu().numpy().astype(np.complex128)
+    X64, y64 = X.astype(np.complex128), y.astype(np.complex128)
+    c32 = c.astype(np.complex64).astype(np.complex128)   # the kernel's coefficients are FP32
+    want = y64 + c32 @ X64
+    scale = np.abs(y64) + np.abs(c32) @ np.abs(X64)
+    assert np.all(np.abs(got - want) <= 2.0 ** -20 * scale)
+    ctx.close()
+
+
 @pytest.mark.parametrize("blas_ds,precision,name", ARITH, ids=[a[2] for a in ARITH])
 def test_multidot_cancellation_and_range(blas_ds, precision, name):
     """y orthogonal to X up to rounding (the case Gram-Schmidt produces), and
