@@ -179,6 +179,10 @@ typedef struct mgeig_params {
                              products, vector updates), at most 64; 0 = the
                              measured defaults: 4 per SM for inner products and
                              FP32 multi-vector updates, 16 for the others        */
+    int guard_coarse_maxiter; /* coarse GMRES iteration cap inside the solves of
+                             Algorithm 1's guard vectors (capped at guard_maxiter
+                             outer steps, they only widen the Rayleigh-Ritz
+                             space); 0 = coarse_maxiter                          */
 } mgeig_params;
 
 /* Work counters and timings of the last setup / eigensolve / solve call. */

@@ -39,6 +39,7 @@ class Params(C.Structure):
         ("adaptive_tol", C.c_int), ("ritz_start", C.c_int), ("coarse_links", C.c_int), ("p_modes", C.c_int),
         ("barrier_timeout", C.c_double), ("coarse_blocks", C.c_int), ("blas_ds", C.c_int),
         ("stencil_ds", C.c_int), ("blas_blocks", C.c_int),
+        ("guard_coarse_maxiter", C.c_int),
     ]
 
 

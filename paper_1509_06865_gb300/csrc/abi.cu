@@ -64,6 +64,7 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (p.blas_ds != 0 && p.blas_ds != 1) return MGEIG_EINVAL;
     if (p.stencil_ds != 0 && p.stencil_ds != 1) return MGEIG_EINVAL;
     if (p.blas_blocks < 0 || p.blas_blocks > 64) return MGEIG_EINVAL;
+    if (p.guard_coarse_maxiter < 0) return MGEIG_EINVAL;
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES && p.smoother != MGEIG_LEARNED) return MGEIG_EINVAL;
@@ -136,6 +137,7 @@ void mgeig_default_params(mgeig_params *p) {
     p->blas_ds = 1;
     p->stencil_ds = 0;
     p->blas_blocks = 0;
+    p->guard_coarse_maxiter = 0;
 }
 
 int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {

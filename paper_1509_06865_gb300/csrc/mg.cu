@@ -72,10 +72,14 @@ constexpr int PB_THREADS = 256;
 constexpr int PB_MAXS = 4;    // sites per thread (aggregates of up to 1024 sites)
 constexpr int PB_MAXN = 24;   // test vectors
 
+// Block Gram-Schmidt of the test vectors on one aggregate and chirality, two
+// passes per vector.  Sums run in the level precision R: in the mixed path the
+// FP64 warp reductions of an earlier form (1/64 of the FP32 rate here) took
+// half of the kernel's time, and P is stored in FP32 anyway.
 template <typename R>
 __global__ void __launch_bounds__(PB_THREADS) interp_kernel(Geom g, AggGeom A, PtrList W, int ntv, MutPtrList P) {
-    __shared__ double sh[PB_THREADS / 32][2 * PB_MAXN];
-    __shared__ double hs[2 * PB_MAXN];
+    __shared__ R sh[PB_THREADS / 32][2 * PB_MAXN];
+    __shared__ R hs[2 * PB_MAXN];
     const int a = blockIdx.x >> 1, chir = blockIdx.x & 1;
     const int V = g.V;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -89,13 +93,13 @@ __global__ void __launch_bounds__(PB_THREADS) interp_kernel(Geom g, AggGeom A, P
     auto reduce = [&](int cnt) {
         __syncthreads();
         for (int i = threadIdx.x; i < 2 * cnt; i += blockDim.x) {
-            double s = 0;
+            R s = 0;
             for (int w = 0; w < nw; ++w) s += sh[w][i];
             hs[i] = s;
         }
         __syncthreads();
     };
-    auto warp_sum = [&](double v) {
+    auto warp_sum = [&](R v) {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     };
@@ -108,12 +112,13 @@ __global__ void __launch_bounds__(PB_THREADS) interp_kernel(Geom g, AggGeom A, P
                 else w[i][k] = cpx<R>();
             }
         for (int pass = 0; pass < 2 && j > 0; ++pass) {
+#pragma unroll 4
             for (int q = 0; q < j; ++q) {
                 const cpx<R> *pq = static_cast<const cpx<R> *>(P.p[q]);
                 cpx<R> d;
                 for (int i = 0; i < ns; ++i)
                     for (int k = 0; k < 6; ++k) cmac_conj(d, Spinor<R>::comp(pq, V, chir * 6 + k, sites[i]), w[i][k]);
-                const double re = warp_sum((double)d.re), im = warp_sum((double)d.im);
+                const R re = warp_sum(d.re), im = warp_sum(d.im);
                 if (lane == 0) { sh[wp][2 * q] = re; sh[wp][2 * q + 1] = im; }
             }
             reduce(j);
@@ -124,13 +129,13 @@ __global__ void __launch_bounds__(PB_THREADS) interp_kernel(Geom g, AggGeom A, P
                     for (int k = 0; k < 6; ++k) w[i][k] = w[i][k] - hc * Spinor<R>::comp(pq, V, chir * 6 + k, sites[i]);
             }
         }
-        double nn = 0;
+        R nn = 0;
         for (int i = 0; i < ns; ++i)
-            for (int k = 0; k < 6; ++k) nn += (double)w[i][k].re * w[i][k].re + (double)w[i][k].im * w[i][k].im;
+            for (int k = 0; k < 6; ++k) nn += w[i][k].re * w[i][k].re + w[i][k].im * w[i][k].im;
         nn = warp_sum(nn);
         if (lane == 0) { sh[wp][0] = nn; sh[wp][1] = 0; }
         reduce(1);
-        const R inv = hs[0] > 0 ? (R)(1.0 / sqrt(hs[0])) : R(0);
+        const R inv = hs[0] > 0 ? R(1) / sqrt(hs[0]) : R(0);
         cpx<R> *dst = static_cast<cpx<R> *>(P.p[j]);
         for (int i = 0; i < ns; ++i)
             for (int k = 0; k < 6; ++k) Spinor<R>::comp(dst, V, chir * 6 + k, sites[i]) = inv * w[i][k];
@@ -484,11 +489,14 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
     float4 *slink = reinterpret_cast<float4 *>(smem_raw + (size_t)B.vol * 12 * sizeof(cpx<R>));   // [vol][4][3]
     constexpr bool stage = sizeof(R) == 4;
     __shared__ R red[3 * 32];   // MR step sums, in the kernel's precision
-    const int b = blockIdx.x;
+    // the grid covers the blocks of one colour: blocks 2i and 2i + 1 differ in
+    // colour (an even number of blocks per direction), CTA i takes the one of
+    // this sweep's colour
+    int b = 2 * blockIdx.x;
     {
         int r = b, bsum = 0;
         for (int mu = 0; mu < 4; ++mu) { bsum += r % B.cdims[mu]; r /= B.cdims[mu]; }
-        if ((bsum & 1) != colour) return;
+        if ((bsum & 1) != colour) b += 1;
     }
     const int V = g.V;
     const int l = threadIdx.x;
@@ -632,8 +640,9 @@ void sap_sweep(Ctx &c, int colour, double sigma, const void *rhs, bool rhs_gamma
     // half the sites: z read+write, rhs, links, clover (from HBM once per sweep)
     const double site_bytes = 12 * 2 * sizeof(R) * 3 + (sizeof(R) == 8 ? 576 : 192) + 72 * sizeof(R);
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_SAP_F64 : K_SAP_F32, site_bytes * c.g.V / 2);
-    sap_kernel<R><<<B.n, threads, smem, c.stream>>>(c.g, B, colour, (R)sigma, U, C, rhs, rhs_gamma5 ? 1 : 0, z,
-                                                    c.prm.sap_mr_iters);
+    MG_REQUIRE(B.cdims[0] % 2 == 0, MGEIG_EINVAL);
+    sap_kernel<R><<<B.n / 2, threads, smem, c.stream>>>(c.g, B, colour, (R)sigma, U, C, rhs, rhs_gamma5 ? 1 : 0, z,
+                                                        c.prm.sap_mr_iters);
     MG_CHECK_LAUNCH();
 }
 

@@ -1098,6 +1098,15 @@ int eigensolve(Ctx &c, int n_want, double tol, double *evals, double *evecs_host
                                    : std::min(c.prm.solve_tol, std::max(0.1 * tol / dls, 1e-12));
             if (c.mixed()) fdefl_prepare<float>(c, sigma, i);
             else fdefl_prepare<double>(c, sigma, i);
+            // a guard vector's solve may take a cheaper coarse solve
+            struct CoarseCap {
+                Ctx &c;
+                int saved;
+                CoarseCap(Ctx &cc, bool guard) : c(cc), saved(cc.prm.coarse_maxiter) {
+                    if (guard && c.prm.guard_coarse_maxiter > 0) c.prm.coarse_maxiter = c.prm.guard_coarse_maxiter;
+                }
+                ~CoarseCap() { c.prm.coarse_maxiter = saved; }
+            } cap{c, is_guard};
             int rc = fgmres_solve(c, sigma, M[i], w.x64.p, tau,
                                   is_guard ? std::min(c.prm.guard_maxiter, c.prm.outer_maxiter) : c.prm.outer_maxiter);
             if (rc != MGEIG_OK && rc != MGEIG_ENOCONV) return rc;
