@@ -220,6 +220,61 @@ def stencil_microbench(ctx, dims, flush, peak_hbm, n=40, nrhs=0):
     return out
 
 
+def coarse_tc_microbench(flush, device, peak_hbm, nrhs=12, n=10):
+    """The coarse operator of the 32^3 x 64 lattice (4^4 aggregates, 20 test
+    vectors: 8192 coarse sites, 40 x 40 blocks; 943 MB in FP32, 472 MB in BF16,
+    out of L2) applied to nrhs coarse vectors: BF16 links with per-link FP32
+    scale on the tensor cores in one launch, against the FP32-link CUDA-core apply
+    one right-hand side after another.  CUDA events on the context's stream, L2
+    flushed before each timed call."""
+    import torch
+
+    import synth
+    from paper_1509_06865_gb300 import LINKS_BF16, LINKS_LEVEL, MIXED, Context
+
+    cfg = workload("north_32x32x32x64")
+    dims = tuple(cfg["dims"])
+    out = {}
+    for links, name in ((LINKS_BF16, "bf16_tensor_cores"), (LINKS_LEVEL, "f32_cuda_cores")):
+        ctx = Context(dims, device=device)
+        ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], agg=cfg["agg"], n_tv=cfg["n_tv"], sap_block=cfg["sap_block"],
+                       precision=MIXED, coarse_links=links, setup_iters=0)
+        ctx.load_gauge(synth.unit_gauge(dims))
+        ctx.setup(cfg["seed"])
+        n2 = 2 * cfg["n_tv"]
+        nc = ctx.coarse_sites * n2
+        X = torch.randn(nrhs * nc, dtype=torch.complex64, device=torch.device("cuda", device))
+        Y = torch.empty_like(X)
+        s = torch.cuda.ExternalStream(ctx.stream())
+        torch.cuda.synchronize()
+
+        def timeit(k):
+            for _ in range(3):
+                ctx.coarse_apply_dev_nrhs(X.data_ptr(), Y.data_ptr(), k, 0.01)
+            times = []
+            for _ in range(n):
+                flush.fill_(2)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                ctx.coarse_apply_dev_nrhs(X.data_ptr(), Y.data_ptr(), k, 0.01)
+                e1.record(s)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            return statistics.median(times)
+
+        link_b = 9 * ctx.coarse_sites * n2 * n2 * (4 if links == LINKS_BF16 else 8)
+        ms_n = timeit(nrhs)
+        ms_1 = timeit(1)
+        byt = link_b + nrhs * 2 * nc * 8
+        out[name] = dict(nrhs=nrhs, ms=ms_n, ms_per_rhs=ms_n / nrhs, ms_one_rhs=ms_1, link_mb=link_b / 1e6,
+                         gbs=byt / (ms_n * 1e-3) / 1e9, frac_hbm=byt / (ms_n * 1e-3) / 1e9 / peak_hbm)
+        ctx.close()
+        del X, Y
+    out["speedup_per_rhs"] = out["f32_cuda_cores"]["ms_per_rhs"] / out["bf16_tensor_cores"]["ms_per_rhs"]
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -277,6 +332,7 @@ def run_gpu(args):
     ctxb.load_gauge(synth.unit_gauge(big))
     sten_big = stencil_microbench(ctxb, big, flush, peaks()["hbm"], n=20, nrhs=12)
     ctxb.close()
+    coarse_tc = coarse_tc_microbench(flush, local, peaks()["hbm"])
     for k in ("f32", "f64"):
         for sd in (sten, sten_big):
             sd[k]["frac_fp64_fma_peak" if k == "f64" else "frac_fp32_fma_peak"] = \
@@ -355,6 +411,7 @@ def run_gpu(args):
         alu_peaks=alu,
         stencil=dict(sten, l2="flushed before every launch", lattice=w["dims"],
                      lattice_32x32x32x64=sten_big),
+        coarse_apply_12rhs_32x32x32x64=coarse_tc,
         roofline=dict(bound="hbm", kernel=top, achieved=achieved, peak=pk["hbm"], unit="GB/s",
                       frac=(achieved / pk["hbm"]) if achieved else None,
                       traffic=DRAM_BYTES_PER_LAUNCH.get(top),
@@ -417,6 +474,50 @@ def north_star(args, flush, device):
                          lambda_max=float(lam[-1]), sweeps=st["sweeps"], solves=st["solves"],
                          outer_iters=st["outer_iters"], coarse_iters=st["coarse_iters"])
     del U_dev
+    return out
+
+
+def learned_study(device=0, steps=2500, batch=4, sigma=0.0):
+    """The learned smoother on the 16^3 x 32 benchmark field: trained on the GPU
+    on steps x batch (residual, SAP correction) pairs the method generates
+    (10^4 by default, the count of the benchmark spec's learned-smoother workload),
+    then one shifted solve (Q - sigma) x = b (b Z2 noise) to 1e-10 by the FP64
+    FGMRES with the two-grid preconditioner whose post-smoother is SAP, the
+    network, or nothing; the true residual is re-computed with the FP64 stencil."""
+    import numpy as np
+
+    import synth
+    from paper_1509_06865_gb300 import LEARNED, MIXED, OP_Q, PREC_F64, SAP, Context
+
+    w = WORKLOAD
+    dims = tuple(w["dims"])
+    U = synth.gauge_field(dims, w["eps"], w["seed"])
+    kw = dict(m0=load_m0(), csw=w["csw"], n_tv=20, precision=MIXED, outer_maxiter=400)
+    ctx = Context(dims, device=device)
+    ctx.set_params(**kw)
+    ctx.load_gauge(U)
+    ctx.setup(w["seed"])
+    ctx.net_init(1)
+    t0 = time.perf_counter()
+    losses = ctx.net_train(steps, batch, 2e-3, 99)
+    t_train = time.perf_counter() - t0
+    b = synth.z2_noise(dims, 1, 21)[0]
+    out = dict(dims=list(dims), pairs=steps * batch, train_s=t_train, loss_first=float(np.mean(losses[:10])),
+               loss_last=float(np.mean(losses[-10:])), sigma=sigma, tol=1e-10)
+    for name, extra in (("sap", dict(smoother=SAP)), ("learned", dict(smoother=LEARNED)),
+                        ("none", dict(smoother=SAP, sap_cycles=0))):
+        ctx.set_params(**kw, **extra)
+        ctx.setup(w["seed"])
+        try:
+            x, st = ctx.solve(b, sigma, 1e-10)
+        except Exception as e:   # a capped solve without smoother reports ENOCONV
+            out[name] = dict(error=str(e))
+            continue
+        r = ctx.apply(x[None], sigma, OP_Q, PREC_F64)[0] - b
+        out[name] = dict(outer_iters=st["outer_iters"], s=st["seconds"], converged=st["converged"],
+                         true_resid=float(np.linalg.norm(r) / np.linalg.norm(b)))
+    ctx.close()
+    print(json.dumps(out), flush=True)
     return out
 
 
@@ -705,10 +806,35 @@ def profile_case(case: str):
     eig16: the 16^3 x 32 benchmark field, multigrid setup with one refinement
     pass, then one sweep of Algorithm 1 on 3 vectors without guards to
     eigen-residual 1e-3: every kernel of the hot path a few hundred times at the
-    benchmark's lattice size, in a few seconds and a few GB of device memory."""
+    benchmark's lattice size, in a few seconds and a few GB of device memory.
+
+    coarse32: three BF16 tensor-core coarse applies on 12 right-hand sides on
+    the coarse grid of the 32^3 x 64 lattice (unit links, setup without
+    iterations), about 6 GB of device memory."""
     import synth
     from paper_1509_06865_gb300 import MIXED, OP_Q, PREC_F32, Context
 
+    if case == "coarse32":
+        # the BF16 tensor-core coarse apply on 12 right-hand sides, 32^3 x 64 coarse grid
+        import torch
+        from paper_1509_06865_gb300 import LINKS_BF16
+        cfg = workload("north_32x32x32x64")
+        dims = tuple(cfg["dims"])
+        ctx = Context(dims)
+        ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], agg=cfg["agg"], n_tv=cfg["n_tv"], sap_block=cfg["sap_block"],
+                       precision=MIXED, coarse_links=LINKS_BF16, setup_iters=0)
+        ctx.load_gauge(synth.unit_gauge(dims))
+        ctx.setup(cfg["seed"])
+        nc = ctx.coarse_sites * 2 * cfg["n_tv"]
+        X = torch.randn(12 * nc, dtype=torch.complex64, device="cuda:0")
+        Y = torch.empty_like(X)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            ctx.coarse_apply_dev_nrhs(X.data_ptr(), Y.data_ptr(), 12, 0.01)
+        torch.cuda.synchronize()
+        ctx.close()
+        print("profile case", case, "ok")
+        return
     if case == "stencil32":
         dims = (32, 32, 32, 64)
         ctx = Context(dims)
@@ -745,9 +871,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-north-star", action="store_true", help="skip the 32^3x64 eigensolve")
     ap.add_argument("--north-star-fp64", action="store_true", help="also the all-FP64 32^3x64 eigensolve")
-    ap.add_argument("--profile-case", choices=["eig16", "stencil32"])
+    ap.add_argument("--profile-case", choices=["eig16", "stencil32", "coarse32"])
     ap.add_argument("--neig-study", action="store_true",
                     help="time Algorithm 1 on the 16^3x32 field for 4..32 wanted pairs and with P from 12 / 6 modes")
+    ap.add_argument("--learned-study", action="store_true",
+                    help="16^3x32: train the learned smoother on 10^4 pairs, then SAP vs net vs none at 1e-10")
     ap.add_argument("--config3-study", action="store_true",
                     help="32^3x64: approximate modes after a 30-iteration setup, then the 50 lowest pairs")
     ap.add_argument("--batch-study", action="store_true",
@@ -768,6 +896,9 @@ def main():
         return
     if args.config3_study:
         config3_study()
+        return
+    if args.learned_study:
+        learned_study()
         return
     if args.impl == "reference":
         run_reference(args)

@@ -307,11 +307,44 @@ struct InLoad<dsf, float> {
     }
 };
 
+// Where a site's links and clover come from: the global arrays, or (FP32, many
+// fields per launch) the CTA's copy in shared memory of its own sites' forward
+// links and clover, in the global layout with V = the CTA's site count, so the
+// same loaders read it.  A backward hop's link is the forward link of the lower
+// neighbour: from the copy when that neighbour is one of the CTA's sites.
+template <typename R>
+struct GlobalFields {
+    const void *U, *clov;
+    int V;
+    // the forward link of the site itself, the backward link (forward link of the lower neighbour)
+    __device__ __forceinline__ void link_fwd(int mu, int site, cpx<R> u[9]) const { Gauge<R>::load(U, V, mu, site, u); }
+    __device__ __forceinline__ void link_bwd(int mu, int site, cpx<R> u[9]) const { Gauge<R>::load(U, V, mu, site, u); }
+    __device__ __forceinline__ void clover(int s, const cpx<R> in[12], cpx<R> out[12]) const {
+        clover_apply<R>(clov, V, s, in, out);
+    }
+};
+
+struct StagedFields {
+    const float4 *sU, *sC;   // [4*3][stride] and [18][stride] float4 planes of the CTA's sites
+    const void *U;           // the global FP32 links, for neighbours outside the CTA
+    int s0, n, stride, V;    // first site, sites staged, plane stride, lattice volume
+    __device__ __forceinline__ void link_fwd(int mu, int site, cpx<float> u[9]) const {
+        Gauge<float>::load(sU, stride, mu, site - s0, u);   // always one of the CTA's sites
+    }
+    __device__ __forceinline__ void link_bwd(int mu, int site, cpx<float> u[9]) const {
+        const int l = site - s0;
+        if (l >= 0 && l < n) Gauge<float>::load(sU, stride, mu, l, u);
+        else Gauge<float>::load(U, V, mu, site, u);
+    }
+    __device__ __forceinline__ void clover(int s, const cpx<float> in[12], cpx<float> out[12]) const {
+        clover_apply<float>(sC, stride, s - s0, in, out);
+    }
+};
+
 // y(s) = op(x)(s) for one site s: the eight hops, the clover term and the shift
-template <typename R, typename Rin, int MODE>
-__device__ __forceinline__ void wilson_clover_site(const Geom &g, const void *__restrict__ U,
-                                                   const void *__restrict__ clov, const void *__restrict__ x,
-                                                   void *__restrict__ y, R sigma, int s) {
+template <typename R, typename Rin, int MODE, typename F>
+__device__ __forceinline__ void wilson_clover_site_f(const Geom &g, const F &fields, const void *__restrict__ x,
+                                                     void *__restrict__ y, R sigma, int s) {
     const int V = g.V;
     int c[4];
     site_coords(g, s, c);
@@ -325,17 +358,17 @@ __device__ __forceinline__ void wilson_clover_site(const Geom &g, const void *__
         int ph;
         cpx<R> u[9], psi[12];
         int n = neighbor(g, s, c, mu, true, &ph);
-        Gauge<R>::load(U, V, mu, s, u);
+        fields.link_fwd(mu, s, u);
         InLoad<R, Rin>::load(x, V, n, psi);
         hop_accumulate<R>(mu, true, u, psi, (R)ph, up, lo);
         n = neighbor(g, s, c, mu, false, &ph);
-        Gauge<R>::load(U, V, mu, n, u);
+        fields.link_bwd(mu, n, u);
         InLoad<R, Rin>::load(x, V, n, psi);
         hop_accumulate<R>(mu, false, u, psi, (R)ph, up, lo);
     }
     cpx<R> psi[12], out[12];
     InLoad<R, Rin>::load(x, V, s, psi);
-    clover_apply<R>(clov, V, s, psi, out);
+    fields.clover(s, psi, out);
     const R half = R(0.5);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -356,6 +389,13 @@ __device__ __forceinline__ void wilson_clover_site(const Geom &g, const void *__
         }
     }
     Spinor<R>::store(y, V, s, out);
+}
+
+template <typename R, typename Rin, int MODE>
+__device__ __forceinline__ void wilson_clover_site(const Geom &g, const void *__restrict__ U,
+                                                   const void *__restrict__ clov, const void *__restrict__ x,
+                                                   void *__restrict__ y, R sigma, int s) {
+    wilson_clover_site_f<R, Rin, MODE>(g, GlobalFields<R>{U, clov, g.V}, x, y, sigma, s);
 }
 
 template <typename R, typename Rin, int MODE>
@@ -381,6 +421,41 @@ __global__ void __launch_bounds__(128) wilson_clover_nrhs_kernel(Geom g, const v
     const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
     wilson_clover_site<R, R, MODE>(g, U, clov, x + rhs * field_bytes, y + rhs * field_bytes, sigma, s);
+}
+
+// FP32, several fields per launch: a CTA of NR_SITES consecutive sites copies
+// its sites' forward links (two rows, 12 float4 planes) and clover (18 planes)
+// into shared memory once, with coalesced loads, and applies the stencil to
+// every field from there; only the spinors (and the backward links of hops that
+// leave the CTA) stream from memory for each field.
+constexpr int NR_SITES = 128;
+constexpr size_t NR_SMEM = (size_t)(12 + 18) * NR_SITES * sizeof(float4);
+
+template <int MODE>
+__global__ void __launch_bounds__(NR_SITES, 3) wilson_clover_nrhs_staged_kernel(
+    Geom g, const float4 *__restrict__ U, const float4 *__restrict__ clov, const char *__restrict__ x,
+    char *__restrict__ y, float sigma, int nrhs, size_t field_bytes) {
+    extern __shared__ float4 nr_smem[];
+    float4 *sU = nr_smem, *sC = nr_smem + 12 * NR_SITES;
+    const int s0 = blockIdx.x * NR_SITES;
+    const int n = min(NR_SITES, g.V - s0);
+    const int t = threadIdx.x;
+    if (t < n) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) sU[q * NR_SITES + t] = U[(size_t)q * g.V + s0 + t];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) sC[q * NR_SITES + t] = clov[(size_t)q * g.V + s0 + t];
+    }
+    __syncthreads();
+    if (t >= n) return;
+    const StagedFields f{sU, sC, U, s0, n, NR_SITES, g.V};
+#pragma unroll 1
+    for (int r = 0; r < nrhs; ++r) {
+        // re-read the staged links and clover for every field instead of holding
+        // all of them in registers across fields (168 of them: occupancy)
+        asm volatile("" ::: "memory");
+        wilson_clover_site_f<float, float, MODE>(g, f, x + r * field_bytes, y + r * field_bytes, sigma, s0 + t);
+    }
 }
 
 template <typename R, typename Rin>
@@ -461,6 +536,30 @@ void apply_fine_nrhs(Ctx &c, int mode, double sigma, const void *x, void *y, int
     c.st.fine_applies += nrhs;
     const char *xb = static_cast<const char *>(x);
     char *yb = static_cast<char *>(y);
+    if (sizeof(R) == 4 && nrhs > 1) {
+        const int nb = grid_for(c.g.V, NR_SITES);
+        const float4 *U4 = c.U32.as<float4>(), *C4 = c.clov32.as<float4>();
+        const float sg = (float)sigma;
+        switch (mode) {
+            case MODE_D:
+                MG_CUDA(cudaFuncSetAttribute(wilson_clover_nrhs_staged_kernel<MODE_D>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NR_SMEM));
+                wilson_clover_nrhs_staged_kernel<MODE_D><<<nb, NR_SITES, NR_SMEM, c.stream>>>(c.g, U4, C4, xb, yb, sg, nrhs, fb);
+                break;
+            case MODE_DSIGMA:
+                MG_CUDA(cudaFuncSetAttribute(wilson_clover_nrhs_staged_kernel<MODE_DSIGMA>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NR_SMEM));
+                wilson_clover_nrhs_staged_kernel<MODE_DSIGMA><<<nb, NR_SITES, NR_SMEM, c.stream>>>(c.g, U4, C4, xb, yb, sg, nrhs, fb);
+                break;
+            default:
+                MG_CUDA(cudaFuncSetAttribute(wilson_clover_nrhs_staged_kernel<MODE_QSIGMA>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NR_SMEM));
+                wilson_clover_nrhs_staged_kernel<MODE_QSIGMA><<<nb, NR_SITES, NR_SMEM, c.stream>>>(c.g, U4, C4, xb, yb, sg, nrhs, fb);
+                break;
+        }
+        MG_CHECK_LAUNCH();
+        return;
+    }
     switch (mode) {
         case MODE_D: wilson_clover_nrhs_kernel<R, MODE_D><<<(int)blocks, threads, 0, c.stream>>>(c.g, U, C, xb, yb, (R)sigma, nrhs, fb); break;
         case MODE_DSIGMA: wilson_clover_nrhs_kernel<R, MODE_DSIGMA><<<(int)blocks, threads, 0, c.stream>>>(c.g, U, C, xb, yb, (R)sigma, nrhs, fb); break;

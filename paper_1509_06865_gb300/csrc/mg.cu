@@ -170,17 +170,37 @@ __global__ void restrict_kernel(Geom g, AggGeom A, PtrList P, int ntv, const voi
     const int V = g.V;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int n2 = 2 * ntv;
-    // each thread visits its sites once per j; sites re-derived per j (cheap)
+    // one site per thread (aggregates of at most blockDim sites, the usual case):
+    // r is loaded once and kept in registers for all test vectors; otherwise each
+    // thread visits its sites once per j
+    const bool one = A.vol <= (int)blockDim.x;
+    int s1 = -1;
+    cpx<R> x1[12];
+    if (one && (int)threadIdx.x < A.vol) {
+        int lc[4];
+        s1 = agg_site(g, A, a, threadIdx.x, lc);
+        Spinor<R>::load(r, V, s1, x1);
+    }
+#pragma unroll 2
     for (int j = 0; j < ntv; ++j) {
         cpx<R> d0, d1;
-        for (int l = threadIdx.x; l < A.vol; l += blockDim.x) {
-            int lc[4];
-            const int s = agg_site(g, A, a, l, lc);
-            cpx<R> x[12], p[12];
-            Spinor<R>::load(r, V, s, x);
-            Spinor<R>::load(P.p[j], V, s, p);
+        if (one) {
+            if (s1 >= 0) {
+                cpx<R> p[12];
+                Spinor<R>::load(P.p[j], V, s1, p);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) { cmac_conj(d0, p[k], x[k]); cmac_conj(d1, p[6 + k], x[6 + k]); }
+                for (int k = 0; k < 6; ++k) { cmac_conj(d0, p[k], x1[k]); cmac_conj(d1, p[6 + k], x1[6 + k]); }
+            }
+        } else {
+            for (int l = threadIdx.x; l < A.vol; l += blockDim.x) {
+                int lc[4];
+                const int s = agg_site(g, A, a, l, lc);
+                cpx<R> x[12], p[12];
+                Spinor<R>::load(r, V, s, x);
+                Spinor<R>::load(P.p[j], V, s, p);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) { cmac_conj(d0, p[k], x[k]); cmac_conj(d1, p[6 + k], x[6 + k]); }
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             d0.re += __shfl_xor_sync(0xffffffffu, d0.re, o); d0.im += __shfl_xor_sync(0xffffffffu, d0.im, o);
