@@ -477,8 +477,8 @@ def north_star(args, flush, device):
     return out
 
 
-def learned_study(device=0, steps=2500, batch=4, sigma=0.0):
-    """The learned smoother on the 16^3 x 32 benchmark field: trained on the GPU
+def learned_study(device=0, steps=2500, batch=4, sigma=0.0, name="bench_16x16x16x32"):
+    """The learned smoother on a workload's field (default the 16^3 x 32 benchmark field): trained on the GPU
     on steps x batch (residual, SAP correction) pairs the method generates
     (10^4 by default, the count of the benchmark spec's learned-smoother workload),
     then one shifted solve (Q - sigma) x = b (b Z2 noise) to 1e-10 by the FP64
@@ -489,10 +489,11 @@ def learned_study(device=0, steps=2500, batch=4, sigma=0.0):
     import synth
     from paper_1509_06865_gb300 import LEARNED, MIXED, OP_Q, PREC_F64, SAP, Context
 
-    w = WORKLOAD
+    w = workload(name)
     dims = tuple(w["dims"])
     U = synth.gauge_field(dims, w["eps"], w["seed"])
-    kw = dict(m0=load_m0(), csw=w["csw"], n_tv=20, precision=MIXED, outer_maxiter=400)
+    kw = dict(m0=w["m0"], csw=w["csw"], n_tv=w["n_tv"], agg=w["agg"], sap_block=w["sap_block"], precision=MIXED,
+              outer_maxiter=400)
     ctx = Context(dims, device=device)
     ctx.set_params(**kw)
     ctx.load_gauge(U)

@@ -424,6 +424,27 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
         }
         __syncthreads();
     };
+    // u[i] = f(i, u[i], sum_l coef1_l X1_l[i], sum_l coef2_l X2_l[i]): two combines
+    // in one pass over the rows and one block barrier
+    auto combine2 = [&](int cnt1, auto vec1, auto coef1, int cnt2, auto vec2, auto coef2, cpx<R> *u, auto f) {
+        const int grp = threadIdx.x / TPR, q = threadIdx.x % TPR, ngrp = blockDim.x / TPR;
+        for (int ib = 0; ib < nr; ib += ngrp) {
+            const int i = ib + grp;
+            cpx<R> a1, a2;
+            if (i < nr) {
+                for (int l = q; l < cnt1; l += TPR) cmac(a1, coef1(l), vec1(l)[i]);
+                for (int l = q; l < cnt2; l += TPR) cmac(a2, coef2(l), vec2(l)[i]);
+            }
+            for (int o = 1; o < TPR; o <<= 1) {
+                a1.re += __shfl_xor_sync(0xffffffffu, a1.re, o);
+                a1.im += __shfl_xor_sync(0xffffffffu, a1.im, o);
+                a2.re += __shfl_xor_sync(0xffffffffu, a2.re, o);
+                a2.im += __shfl_xor_sync(0xffffffffu, a2.im, o);
+            }
+            if (i < nr && q == 0) u[i] = f(i, u[i], a1, a2);
+        }
+        __syncthreads();
+    };
     auto publish = [&](const cpx<R> *v) {
         for (int i = threadIdx.x; i < nr; i += blockDim.x) a.pub[r0 + i] = v[i];
     };
@@ -557,13 +578,14 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs<R> a
             }
             __syncthreads();
             // w1 = g5 (u - A W t) - sum_i h1_i s_i V_i, published for the next matvec
-            combine(k, AWv, tcoef, ws, [&](int i, cpx<R>, cpx<R> s) { return g5(i, uj[i] - s); });
-            combine(j + 1, Vv, [&](int i) { return cpx<R>((R)(h1[i].x * scale[i]), (R)(h1[i].y * scale[i])); }, ws,
-                    [](int, cpx<R> wi, cpx<R> s) { return wi - s; });
+            combine2(k, AWv, tcoef, j + 1, Vv,
+                     [&](int i) { return cpx<R>((R)(h1[i].x * scale[i]), (R)(h1[i].y * scale[i])); }, ws,
+                     [&](int i, cpx<R>, cpx<R> s1, cpx<R> s2) { return g5(i, uj[i] - s1) - s2; });
             publish(ws);
             // reduction 2: h2_i = <s_i V_i, w1>, ||w1||^2
             dots(j + 1, 0, Vv, [&](int i) { return scale[i]; }, ws, false);
-            norm_part(ws, j + 1);
+            // ||w1||^2 as one more inner product (no extra block barrier)
+            dots(1, j + 1, [&](int) -> const cpx<R> * { return ws; }, one, ws, false);
             if (!reduce(OFF_S2, j + 2)) return;
             if (threadIdx.x == 0) {
                 R n2s = h[j + 1].x;

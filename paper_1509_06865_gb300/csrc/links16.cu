@@ -177,18 +177,32 @@ coarse_apply_nrhs_tc_kernel(int nagg, int ntv, int nrhs, int NT, const __nv_bflo
     }
     asm volatile("cp.async.commit_group;\n" ::);
     for (int e = threadIdx.x; e < TC_SLACK; e += blockDim.x) As[9 * 2 * plane + e] = __float2bfloat16_rn(0.f);
-    // 2. right-hand sides of the nine neighbours, scaled by the link's scale, in BF16
-    for (int e = threadIdx.x; e < 9 * ncols * 48; e += blockDim.x) {
-        const int k = e % 48, col = (e / 48) % ncols, d = e / (48 * ncols);
-        float v = 0.f;
-        const int r = col < nrhs ? col : col - nrhs;
-        if (k < n2 && col < 2 * nrhs) {
+    // 2. right-hand sides of the nine neighbours, scaled by the link's scale, in BF16:
+    //    warp-strided over (hop d, right-hand side r), lanes over the rows k; one
+    //    float2 load fills column r (real parts) and column nrhs + r (imaginary)
+    {
+        const int wq = threadIdx.x >> 5, lq = threadIdx.x & 31, nwq = blockDim.x >> 5;
+        for (int dr = wq; dr < 9 * nrhs; dr += nwq) {
+            const int d = dr / nrhs, r = dr - d * nrhs;
             const size_t blk = (size_t)d * nagg + site;
             const int b = __ldg(nbr + blk);
-            const float2 xv = X[((size_t)r * nagg + b) * n2 + k];
-            v = __ldg(scale + blk) * (col < nrhs ? xv.x : xv.y);
+            const float sc = __ldg(scale + blk);
+            const float2 *xr = X + ((size_t)r * nagg + b) * n2;
+            __nv_bfloat16 *br = Bs + ((size_t)d * ncols + r) * TC_BP;
+            __nv_bfloat16 *bi = Bs + ((size_t)d * ncols + nrhs + r) * TC_BP;
+            for (int k = lq; k < 48; k += 32) {
+                float2 xv = make_float2(0.f, 0.f);
+                if (k < n2) xv = xr[k];
+                br[k] = __float2bfloat16_rn(sc * xv.x);
+                bi[k] = __float2bfloat16_rn(sc * xv.y);
+            }
         }
-        Bs[((size_t)d * ncols + col) * TC_BP + k] = __float2bfloat16_rn(v);
+        // the padding columns 2 nrhs .. 8 NT - 1 of every hop are zero
+        const int npad = ncols - 2 * nrhs;
+        for (int e = threadIdx.x; e < 9 * npad * 48; e += blockDim.x) {
+            const int k = e % 48, q = e / 48, d = q / npad, col = 2 * nrhs + q % npad;
+            Bs[((size_t)d * ncols + col) * TC_BP + k] = __float2bfloat16_rn(0.f);
+        }
     }
     asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
