@@ -232,7 +232,7 @@ def coarse_tc_microbench(flush, device, peak_hbm, nrhs=12, n=10):
     import synth
     from paper_1509_06865_gb300 import LINKS_BF16, LINKS_LEVEL, MIXED, Context
 
-    cfg = workload("north_32x32x32x64")
+    cfg = workload("large_32x32x32x64")
     dims = tuple(cfg["dims"])
     out = {}
     for links, name in ((LINKS_BF16, "bf16_tensor_cores"), (LINKS_LEVEL, "f32_cuda_cores")):
@@ -383,7 +383,7 @@ def run_gpu(args):
                     max_abs_diff_vs_mixed=float(np.max(np.abs(np.asarray(lam) - np.asarray(lam64)))))
 
     # the 20 lowest pairs of the 32^3 x 64 field (one step each, after the timed region)
-    north = None if args.no_north_star else north_star(args, flush, local)
+    large = None if args.no_large else large_field(args, flush, local)
     # like for like: the GPU eigensolve of the 4^4 field on which the CPU baseline
     # times the oracle's complete eigensolve
     small = small_field(flush, local)
@@ -406,7 +406,7 @@ def run_gpu(args):
         result=dict(lambda_min=float(lam[0]), lambda_max=float(lam[-1]), max_resid=float(max(res)),
                     sweeps=st["sweeps"], solves=st["solves"], outer_iters=st["outer_iters"],
                     mg_cycles=st["mg_cycles"], coarse_iters=st["coarse_iters"]),
-        north_star_32x32x32x64=north,
+        eigensolve_32x32x32x64=large,
         like_for_like_4x4x4x4=small,
         alu_peaks=alu,
         stencil=dict(sten, l2="flushed before every launch", lattice=w["dims"],
@@ -435,16 +435,16 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
-def north_star(args, flush, device):
+def large_field(args, flush, device):
     """The 20 lowest pairs of Q on the 32^3 x 64 field to 1e-10 (mixed, and FP64
-    with --north-star-fp64), one step each, CUDA events around the step."""
+    with --large-fp64), one step each, CUDA events around the step."""
     import numpy as np
     import torch
 
     import synth
     from paper_1509_06865_gb300 import FP64, MIXED, Context
 
-    cfg = workload("north_32x32x32x64")
+    cfg = workload("large_32x32x32x64")
     if cfg["m0"] is None:
         return dict(skipped="m0 of the 32^3x64 workload not tuned")
     dims = tuple(cfg["dims"])
@@ -454,7 +454,7 @@ def north_star(args, flush, device):
                         f"{cfg['n_eig']} lowest eigenpairs of Q to resid {cfg['tol']}",
                dims=cfg["dims"], m0=cfg["m0"], n_eig=cfg["n_eig"], tol=cfg["tol"])
     for prec, name in ((MIXED, "mixed"), (FP64, "fp64")):
-        if prec == FP64 and not args.north_star_fp64:
+        if prec == FP64 and not args.large_fp64:
             continue
         ctx = Context(dims, device=device)
         ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
@@ -480,7 +480,7 @@ def north_star(args, flush, device):
 def learned_study(device=0, steps=2500, batch=4, sigma=0.0, name="bench_16x16x16x32"):
     """The learned smoother on a workload's field (default the 16^3 x 32 benchmark field): trained on the GPU
     on steps x batch (residual, SAP correction) pairs the method generates
-    (10^4 by default, the count of the benchmark spec's learned-smoother workload),
+    (10^4 by default, the training-set size of the learned-smoother workload),
     then one shifted solve (Q - sigma) x = b (b Z2 noise) to 1e-10 by the FP64
     FGMRES with the two-grid preconditioner whose post-smoother is SAP, the
     network, or nothing; the true residual is re-computed with the FP64 stencil."""
@@ -532,7 +532,7 @@ def config3_study(device=0, n_eig=50, setup_iters=30):
     import synth
     from paper_1509_06865_gb300 import LINKS_BF16, MIXED, Context
 
-    cfg = workload("north_32x32x32x64")
+    cfg = workload("large_32x32x32x64")
     dims = tuple(cfg["dims"])
     ctx = Context(dims, device=device)
     ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
@@ -819,7 +819,7 @@ def profile_case(case: str):
         # the BF16 tensor-core coarse apply on 12 right-hand sides, 32^3 x 64 coarse grid
         import torch
         from paper_1509_06865_gb300 import LINKS_BF16
-        cfg = workload("north_32x32x32x64")
+        cfg = workload("large_32x32x32x64")
         dims = tuple(cfg["dims"])
         ctx = Context(dims)
         ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], agg=cfg["agg"], n_tv=cfg["n_tv"], sap_block=cfg["sap_block"],
@@ -870,8 +870,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-north-star", action="store_true", help="skip the 32^3x64 eigensolve")
-    ap.add_argument("--north-star-fp64", action="store_true", help="also the all-FP64 32^3x64 eigensolve")
+    ap.add_argument("--no-large", action="store_true", help="skip the 32^3x64 eigensolve")
+    ap.add_argument("--large-fp64", action="store_true", help="also the all-FP64 32^3x64 eigensolve")
     ap.add_argument("--profile-case", choices=["eig16", "stencil32", "coarse32"])
     ap.add_argument("--neig-study", action="store_true",
                     help="time Algorithm 1 on the 16^3x32 field for 4..32 wanted pairs and with P from 12 / 6 modes")

@@ -80,7 +80,7 @@ extern "C" {
 #define MGEIG_PREC_F32_F64_DS 3   /* x FP32, y FP64 (the outer FGMRES matvec)      */
 
 /* storage of the coarse operator's links in the mixed-precision preconditioner
- * (spec extension of the Sec. 2.2 precision split: the coarse operator in
+ * (an extension of the Sec. 2.2 precision split beyond the paper: the coarse operator in
  * 16 bits with one FP32 scale per 2N_tv x 2N_tv link block, FP32 arithmetic) */
 #define MGEIG_LINKS_LEVEL 0   /* the level precision (FP32 in MGEIG_MIXED)            */
 #define MGEIG_LINKS_BF16 1    /* bfloat16 entries / per-link FP32 scale               */
@@ -462,7 +462,7 @@ int mgeig_lma_apply(mgeig_ctx *ctx, int mode, const double *x, double *y);
 int mgeig_lma_loop_high(mgeig_ctx *ctx, int nstoch, uint64_t seed, double tol, double *Lhigh, mgeig_stats *stats);
 
 /* ---------------------------------------------------------------------------
- * The learned smoother (the paper has none; spec extension of the
+ * The learned smoother (the paper has none; an extension of the
  * smoother M of Eq. 2.3): a 3-layer 4D convolutional network (3^4 taps,
  * 24 -> 32 -> 32 -> 24 real channels, no bias, GELU in its tanh form between
  * the layers), applied as M(r) = ||r|| f(r / ||r||), trained on the GPU with the

@@ -149,14 +149,15 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 
 // Shared memory of one CTA (one coarse site), n2 = 2 N_tv <= 48 rows:
-//   As  the nine blocks' planes as stored in global memory ([d][re|im][row][col],
-//       n2 x n2 each, row pitch n2 halves), plus TC_SLACK zero halves: the row
-//       and column tiles run to the next multiple of 16, the extra columns read
-//       finite entries of the next row that meet zero rows of B, and the extra
-//       rows are dropped
+//   As  a ring of two hop buffers: one link block's planes as stored in global
+//       memory ([re|im][row][col], n2 x n2 each, row pitch n2 halves) plus TC_SLACK
+//       zero halves (the row and column tiles run to the next multiple of 16, the
+//       extra columns read finite entries of the next row that meet zero rows of
+//       B, and the extra rows are dropped).  Hop d + 1 is copied (cp.async) while
+//       hop d is multiplied
 //   Bs  [d][column n < 8 NT][k < 48] staged s_d [Xr | Xi], zero for k >= n2
 //   Cs  (after the products) [plane][48][2 nrhs] accumulators
-__global__ void __launch_bounds__(TC_THREADS, 2)
+__global__ void __launch_bounds__(TC_THREADS, 5)
 coarse_apply_nrhs_tc_kernel(int nagg, int ntv, int nrhs, int NT, const __nv_bfloat16 *__restrict__ L,
                             const float *__restrict__ scale, const int *__restrict__ nbr, float sigma,
                             const float2 *__restrict__ X, float2 *__restrict__ Y) {
@@ -165,18 +166,24 @@ coarse_apply_nrhs_tc_kernel(int nagg, int ntv, int nrhs, int NT, const __nv_bflo
     const int site = blockIdx.x;
     const size_t plane = (size_t)n2 * n2;
     __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(tc_smem);
-    const size_t as_elems = 9 * 2 * plane + TC_SLACK;
-    __nv_bfloat16 *Bs = As + ((as_elems + 7) / 8) * 8;
+    const size_t hop_elems = ((2 * plane + TC_SLACK + 7) / 8) * 8;   // one ring buffer (16-byte multiple)
+    __nv_bfloat16 *Bs = As + 2 * hop_elems;
     const int ncols = 8 * NT;
-    // 1. the nine link blocks (contiguous 2 n2^2 halves each) by 16-byte async copies
+    // 1. the link block of hop d (contiguous 2 n2^2 halves) into ring buffer d & 1
+    //    by 16-byte async copies, one commit group per hop
     const int chunks_per_blk = (int)(2 * plane * 2 / 16);
-    for (int e = threadIdx.x; e < 9 * chunks_per_blk; e += blockDim.x) {
-        const int d = e / chunks_per_blk, q = e % chunks_per_blk;
+    auto copy_hop = [&](int d) {
         const __nv_bfloat16 *src = L + ((size_t)d * nagg + site) * 2 * plane;
-        cp_async16(As + (size_t)d * 2 * plane + (size_t)q * 8, src + (size_t)q * 8);
+        __nv_bfloat16 *dst = As + (size_t)(d & 1) * hop_elems;
+        for (int q = threadIdx.x; q < chunks_per_blk; q += blockDim.x)
+            cp_async16(dst + (size_t)q * 8, src + (size_t)q * 8);
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+    copy_hop(0);
+    for (int e = threadIdx.x; e < TC_SLACK; e += blockDim.x) {
+        As[2 * plane + e] = __float2bfloat16_rn(0.f);
+        As[hop_elems + 2 * plane + e] = __float2bfloat16_rn(0.f);
     }
-    asm volatile("cp.async.commit_group;\n" ::);
-    for (int e = threadIdx.x; e < TC_SLACK; e += blockDim.x) As[9 * 2 * plane + e] = __float2bfloat16_rn(0.f);
     // 2. right-hand sides of the nine neighbours, scaled by the link's scale, in BF16:
     //    warp-strided over (hop d, right-hand side r), lanes over the rows k; one
     //    float2 load fills column r (real parts) and column nrhs + r (imaginary)
@@ -204,17 +211,23 @@ coarse_apply_nrhs_tc_kernel(int nagg, int ntv, int nrhs, int NT, const __nv_bflo
             Bs[((size_t)d * ncols + col) * TC_BP + k] = __float2bfloat16_rn(0.f);
         }
     }
-    asm volatile("cp.async.wait_all;\n" ::);
-    __syncthreads();
     // 3. products: warp w takes rows 16 (w / 2) .. +15 of plane w % 2, every column tile
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
     const int mt = w >> 1, pl = w & 1;
     float acc[TC_MAXNT][4];
 #pragma unroll
     for (int j = 0; j < TC_MAXNT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    if (16 * mt < n2) {
-        for (int d = 0; d < 9; ++d) {
-            const __nv_bfloat16 *Ap = As + ((size_t)d * 2 + pl) * plane;
+    for (int d = 0; d < 9; ++d) {
+        // hop d + 1 streams in while hop d is multiplied
+        if (d + 1 < 9) {
+            copy_hop(d + 1);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        __syncthreads();   // hop d (and, for d = 0, the staged B and the slack) visible to all
+        if (16 * mt < n2) {
+            const __nv_bfloat16 *Ap = As + (size_t)(d & 1) * hop_elems + (size_t)pl * plane;
             const __nv_bfloat16 *Bp = Bs + (size_t)d * ncols * TC_BP;
             for (int ks = 0; ks < 3 && 16 * ks < n2; ++ks) {
                 uint32_t a[4];
@@ -235,8 +248,9 @@ coarse_apply_nrhs_tc_kernel(int nagg, int ntv, int nrhs, int NT, const __nv_bflo
                 }
             }
         }
+        __syncthreads();   // every read of ring buffer d & 1 is done before hop d + 2 overwrites it
     }
-    __syncthreads();   // every read of As / Bs is done: the accumulators reuse the space
+    // every read of As / Bs is done (the last barrier of the loop): the accumulators reuse the space
     float *Cs = reinterpret_cast<float *>(tc_smem);   // [plane][48][ncols]
     if (16 * mt < n2) {
 #pragma unroll
@@ -266,8 +280,8 @@ coarse_apply_nrhs_tc_kernel(int nagg, int ntv, int nrhs, int NT, const __nv_bflo
 }
 
 size_t coarse_nrhs_tc_smem(int n2, int NT) {
-    const size_t as_elems = 9 * 2 * (size_t)n2 * n2 + TC_SLACK;
-    const size_t a = ((as_elems + 7) / 8) * 8 * 2;
+    const size_t hop_elems = ((2 * (size_t)n2 * n2 + TC_SLACK + 7) / 8) * 8;
+    const size_t a = 2 * hop_elems * 2;
     const size_t b = (size_t)9 * 8 * NT * TC_BP * 2;
     const size_t cbytes = (size_t)2 * 48 * 8 * NT * 4;
     return std::max(a + b, cbytes);
