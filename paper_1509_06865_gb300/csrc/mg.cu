@@ -505,8 +505,11 @@ __global__ void __launch_bounds__(256, SapBounds<R>::minb)
 sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
            const void *__restrict__ clov, const void *__restrict__ rhs, int rhs_g5, void *z, int mr_iters) {
     extern __shared__ unsigned char smem_raw[];
-    cpx<R> *rho = reinterpret_cast<cpx<R> *>(smem_raw);       // [vol][12]
-    float4 *slink = reinterpret_cast<float4 *>(smem_raw + (size_t)B.vol * 12 * sizeof(cpx<R>));   // [vol][4][3]
+    // component-major (rho[k][vol], slink[mu][3][vol]): consecutive threads read
+    // consecutive words, without the 4-way bank conflicts of a site-major layout
+    cpx<R> *rho = reinterpret_cast<cpx<R> *>(smem_raw);       // [12][vol]
+    float4 *slink = reinterpret_cast<float4 *>(smem_raw + (size_t)B.vol * 12 * sizeof(cpx<R>));   // [4][3][vol]
+    const int bv = B.vol;
     constexpr bool stage = sizeof(R) == 4;
     __shared__ R red[3 * 32];   // MR step sums, in the kernel's precision
     // the grid covers the blocks of one colour: blocks 2i and 2i + 1 differ in
@@ -532,7 +535,7 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
     if (stage && active) {
         const float4 *ug = static_cast<const float4 *>(U);
         for (int mu = 0; mu < 4; ++mu)
-            for (int e = 0; e < 3; ++e) slink[(l * 4 + mu) * 3 + e] = ug[((size_t)mu * 3 + e) * V + s];
+            for (int e = 0; e < 3; ++e) slink[(mu * 3 + e) * bv + l] = ug[((size_t)mu * 3 + e) * V + s];
     }
     // residual of D_sigma z = rhs on this block (z read with its global neighbours)
     if (active) {
@@ -562,8 +565,8 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
             cpx<R> du = dz[k] - half * up[k] - sigma * zs[k];
             cpx<R> dl = dz[6 + k] - half * lo[k] + sigma * zs[6 + k];
             cpx<R> bu = bb[k], bl = rhs_g5 ? -bb[6 + k] : bb[6 + k];
-            rho[l * 12 + k] = bu - du;
-            rho[l * 12 + 6 + k] = bl - dl;
+            rho[k * bv + l] = bu - du;
+            rho[(6 + k) * bv + l] = bl - dl;
         }
     }
     __syncthreads();
@@ -587,8 +590,8 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
                                                                                               : B.agg[0] * B.agg[1] * B.agg[2]);
                     cpx<R> u[9], psi[12];
                     if constexpr (stage) {
-                        const float4 *q = slink + ((fwd ? l : ln) * 4 + mu) * 3;
-                        const float4 a = q[0], b = q[1], cc = q[2];
+                        const float4 *q = slink + (size_t)mu * 3 * bv + (fwd ? l : ln);
+                        const float4 a = q[0], b = q[bv], cc = q[2 * bv];
                         u[0] = cpx<R>(a.x, a.y); u[1] = cpx<R>(a.z, a.w); u[2] = cpx<R>(b.x, b.y);
                         u[3] = cpx<R>(b.z, b.w); u[4] = cpx<R>(cc.x, cc.y); u[5] = cpx<R>(cc.z, cc.w);
                         u[6] = conj(u[1] * u[5] - u[2] * u[4]);
@@ -600,12 +603,12 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
                         Gauge<R>::load(U, V, mu, fwd ? s : n, u);
                     }
 #pragma unroll
-                    for (int k = 0; k < 12; ++k) psi[k] = rho[ln * 12 + k];
+                    for (int k = 0; k < 12; ++k) psi[k] = rho[k * bv + ln];
                     hop_accumulate<R>(mu, fwd, u, psi, (R)1, up, lo);
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 12; ++k) rl[k] = rho[l * 12 + k];
+            for (int k = 0; k < 12; ++k) rl[k] = rho[k * bv + l];
             clover_apply<R>(clov, V, s, rl, q);
             const R half = R(0.5);
 #pragma unroll
@@ -634,7 +637,7 @@ sap_kernel(Geom g, AggGeom B, int colour, R sigma, const void *__restrict__ U,
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
                 cmac(e[k], alpha, rl[k]);
-                rho[l * 12 + k] = rl[k] - alpha * q[k];
+                rho[k * bv + l] = rl[k] - alpha * q[k];
             }
         }
         __syncthreads();
