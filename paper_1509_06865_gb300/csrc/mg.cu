@@ -340,7 +340,10 @@ __global__ void __launch_bounds__(CB_THREADS) coarse_build_kernel(Geom g, AggGeo
     extern __shared__ unsigned char smem_raw[];
     const int a = blockIdx.x / 9, d = blockIdx.x % 9;
     const int n2 = 2 * ntv;
-    cpx<R> *sP = reinterpret_cast<cpx<R> *>(smem_raw);           // [CHUNK][ntv][12]
+    // component-major within a staged site ([CHUNK][12][ntv]): the threads of a warp
+    // take consecutive rows, i.e. consecutive test vectors, so their reads of sP are
+    // consecutive words (a [CHUNK][ntv][12] layout had 4-way bank conflicts)
+    cpx<R> *sP = reinterpret_cast<cpx<R> *>(smem_raw);           // [CHUNK][12][ntv]
     cpx<R> *sH = sP + (size_t)CB_CHUNK * ntv * 12;               // [CHUNK][n2][12]
     const int V = g.V;
     // sites of this direction: all sites (d = 0) or the face l_mu = agg-1 / 0
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(CB_THREADS) coarse_build_kernel(Geom g, AggGeo
             cpx<R> v[12];
             if (item < ntv) {
                 Spinor<R>::load(P.p[item], V, s, v);
-                for (int k = 0; k < 12; ++k) sP[((size_t)sl * ntv + item) * 12 + k] = v[k];
+                for (int k = 0; k < 12; ++k) sP[((size_t)sl * 12 + k) * ntv + item] = v[k];
             } else {
                 const int col = item - ntv, cp = col / ntv, jp = col % ntv;
                 directional_column<R>(g, A, U, clov, P.p[jp], cp, d, s, c, v);
@@ -395,10 +398,10 @@ __global__ void __launch_bounds__(CB_THREADS) coarse_build_kernel(Geom g, AggGeo
                 const int cr = row / ntv, jr = row % ntv;
                 cpx<R> t = acc[q];
                 for (int sl = 0; sl < cnt; ++sl) {
-                    const cpx<R> *pr = sP + ((size_t)sl * ntv + jr) * 12 + cr * 6;
+                    const cpx<R> *pr = sP + ((size_t)sl * 12 + cr * 6) * ntv + jr;   // component k at pr[k * ntv]
                     const cpx<R> *hc = sH + ((size_t)sl * n2 + col) * 12 + cr * 6;
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) cmac_conj(t, pr[k], hc[k]);
+                    for (int k = 0; k < 6; ++k) cmac_conj(t, pr[(size_t)k * ntv], hc[k]);
                 }
                 acc[q] = t;
             }
