@@ -43,9 +43,9 @@ static bool vec4_ok(const PtrPack &pk, int k, const void *y, size_t n) {
 // GB300 (16 FP32 or 8 double-float vectors per launch): 4 per SM beat 1024
 // blocks by 1.1-1.35x at 16^3 x 32 and 32^3 x 64 (fewer block epilogues and
 // partial sums)
-static int red_grid(const Ctx &c, size_t n) {
+static int red_grid(const Ctx &c, size_t n, int per_sm = 4) {
     size_t b = (n + RED_THREADS * 4 - 1) / (RED_THREADS * 4);
-    b = std::min<size_t>(b, (size_t)c.sms * (c.prm.blas_blocks > 0 ? c.prm.blas_blocks : 4));
+    b = std::min<size_t>(b, (size_t)c.sms * (c.prm.blas_blocks > 0 ? c.prm.blas_blocks : per_sm));
     if (b < 1) b = 1;
     if (b > RED_MAXBLOCKS) b = RED_MAXBLOCKS;
     return (int)b;
@@ -286,7 +286,10 @@ static double2 *partial_ptr(Ctx &c) { return c.red_partial.as<double2>(); }
 
 template <typename R>
 void blas_multidot(Ctx &c, const void *const *X, int k, const void *y, size_t n, cpx<double> *d_out) {
-    const int nb = red_grid(c, n);
+    // FP32 vectors below 8 M complex values (a 16^3 x 32 spinor is 1.6 M): 2 blocks
+    // per SM, 1.3x faster there than 4 (measured); the longer ones and the
+    // double-float kernels run best at 4
+    const int nb = red_grid(c, n, (sizeof(R) == 4 && n < ((size_t)8 << 20)) ? 2 : 4);
     const size_t pstride = RED_MAXBLOCKS;
     TimeScope ts(c.timer, sizeof(R) == 8 ? K_BLAS_F64 : K_BLAS_LOW, (double)(k + 1) * n * 2 * sizeof(R));
     const bool ds = sizeof(R) == 8 && c.ds_blas();
