@@ -809,12 +809,30 @@ def profile_case(case: str):
     eigen-residual 1e-3: every kernel of the hot path a few hundred times at the
     benchmark's lattice size, in a few seconds and a few GB of device memory.
 
+    learned16: four training steps of the learned smoother (batch 4) on the
+    16^3 x 32 field: the BF16 tensor-core convolutions forward, data and weight
+    gradients, about 3 GB of device memory.
+
     coarse32: three BF16 tensor-core coarse applies on 12 right-hand sides on
     the coarse grid of the 32^3 x 64 lattice (unit links, setup without
     iterations), about 6 GB of device memory."""
     import synth
     from paper_1509_06865_gb300 import MIXED, OP_Q, PREC_F32, Context
 
+    if case == "learned16":
+        # the learned smoother's training and inference kernels on the 16^3 x 32 field
+        w = workload("bench_16x16x16x32")
+        dims = tuple(w["dims"])
+        ctx = Context(dims)
+        ctx.set_params(m0=w["m0"], csw=w["csw"], n_tv=w["n_tv"], agg=w["agg"], sap_block=w["sap_block"],
+                       precision=MIXED, setup_iters=1)
+        ctx.load_gauge(synth.gauge_field(dims, w["eps"], w["seed"]))
+        ctx.setup(w["seed"])
+        ctx.net_init(1)
+        ctx.net_train(4, 4, 2e-3, 99)
+        ctx.close()
+        print("profile case", case, "ok")
+        return
     if case == "coarse32":
         # the BF16 tensor-core coarse apply on 12 right-hand sides, 32^3 x 64 coarse grid
         import torch
@@ -872,7 +890,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 32^3x64 eigensolve")
     ap.add_argument("--large-fp64", action="store_true", help="also the all-FP64 32^3x64 eigensolve")
-    ap.add_argument("--profile-case", choices=["eig16", "stencil32", "coarse32"])
+    ap.add_argument("--profile-case", choices=["eig16", "stencil32", "coarse32", "learned16"])
     ap.add_argument("--neig-study", action="store_true",
                     help="time Algorithm 1 on the 16^3x32 field for 4..32 wanted pairs and with P from 12 / 6 modes")
     ap.add_argument("--learned-study", action="store_true",
