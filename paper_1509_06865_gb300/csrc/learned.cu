@@ -131,6 +131,12 @@ struct ConvArgs {
     int cout;                    // output channels that are kept (the rest written as zero)
 };
 
+// Staged rows of 32 BF16 channels are 64 bytes, four 16-byte chunks.  An 8-row
+// ldmatrix phase over consecutive rows would hit each bank four times, so chunk c
+// of row r is stored at chunk c ^ ((r >> 1) & 3): rows 2k and 2k + 1 share a
+// pattern, four row pairs cover the 32 banks.
+__device__ __forceinline__ int swz(int row, int chunk) { return row * NC + 8 * (chunk ^ ((row >> 1) & 3)); }
+
 // out(s)[o] = sum_tap sum_i W[tap][o][i] in(s + tap)[i] for one box of sites
 template <int EPI>
 __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
         x[1] = wrap(o[1] + h % HY - 1, a.D.L[1]); h /= HY;
         x[2] = wrap(o[2] + h % HZ - 1, a.D.L[2]);
         x[3] = wrap(o[3] + h / HZ - 1, a.D.L[3]);
-        cp_async16(halo + (size_t)(e >> 2) * NC + ch * 8, a.in + site_index(a.D, field, x) * NC + ch * 8);
+        cp_async16(halo + swz(e >> 2, ch), a.in + site_index(a.D, field, x) * NC + ch * 8);
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float acc[2][4][4];
@@ -165,13 +171,12 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
     for (int t0 = 0; t0 < NTAPS; t0 += TAPS_PER_STAGE) {
         __syncthreads();   // the previous weights are no longer read
         for (int e = threadIdx.x; e < TAPS_PER_STAGE * NC * NC / 8; e += blockDim.x)
-            cp_async16(wst + (size_t)e * 8, a.W + (size_t)t0 * NC * NC + (size_t)e * 8);
+            cp_async16(wst + swz(e >> 2, e & 3), a.W + (size_t)t0 * NC * NC + (size_t)e * 8);
         cp_async_wait_all();
         __syncthreads();
         for (int tt = 0; tt < TAPS_PER_STAGE; ++tt) {
             int d[4];
             tap_offset(t0 + tt, d);
-            const __nv_bfloat16 *wt = wst + (size_t)tt * NC * NC;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 uint32_t af[2][4];
@@ -179,12 +184,12 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
                 for (int mi = 0; mi < 2; ++mi) {
                     const int h = (((lc[mi][3] + 1 + d[3]) * HZ + (lc[mi][2] + 1 + d[2])) * HY +
                                    (lc[mi][1] + 1 + d[1])) * HX + (lc[mi][0] + 1 + d[0]);
-                    ldmatrix_x4(af[mi], halo + (size_t)h * NC + 16 * ks + a_ch);
+                    ldmatrix_x4(af[mi], halo + swz(h, 2 * ks + (a_ch >> 3)));
                 }
 #pragma unroll
                 for (int np = 0; np < 2; ++np) {
                     uint32_t bf[4];
-                    ldmatrix_x4(bf, wt + (size_t)(16 * np + b_row) * NC + 16 * ks + b_k);
+                    ldmatrix_x4(bf, wst + swz(tt * NC + 16 * np + b_row, 2 * ks + (b_k >> 3)));
 #pragma unroll
                     for (int mi = 0; mi < 2; ++mi) {
                         mma16816(acc[mi][2 * np], af[mi], bf[0], bf[1]);
