@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -386,7 +387,7 @@ def run_gpu(args):
     large = None if args.no_large else large_field(args, flush, local)
     # like for like: the GPU eigensolve of the 4^4 field on which the CPU baseline
     # times the oracle's complete eigensolve
-    small = small_field(flush, local)
+    small, small_pairs = small_field(flush, local)
 
     if rank != 0:
         return
@@ -427,11 +428,17 @@ def run_gpu(args):
         kernels_note="per-class device time of one step (the last warm-up step, every class timed)",
     )
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_baseline_subprocess()
+        vec_path = os.path.join(tempfile.mkdtemp(prefix="mgeig_oracle_"), "V.npy")
+        line["cpu_baseline"] = oracle_baseline_subprocess(vec_path)
         cs = line["cpu_baseline"].get("complete_4x4x4x4")
         if cs:
             small["oracle_s"] = cs["wall_s"]
             small["oracle_over_gpu"] = cs["wall_s"] / small["gpu_s"]
+            # the error of the GPU's result against the FP64 oracle's
+            try:
+                small["vs_oracle"] = pairs_vs_oracle(small_pairs[0], small_pairs[1], cs["lam"], np.load(vec_path))
+            except Exception as e:  # the line is printed whatever this comparison meets
+                small["vs_oracle"] = dict(error=repr(e)[:300])
     print(json.dumps(line), flush=True)
 
 
@@ -586,8 +593,36 @@ def small_field(flush, device):
         torch.cuda.synchronize()
         ctx.close()
         times.append(e0.elapsed_time(e1) / 1e3)
+    # the same eigensolve once more, untimed, for the eigenvectors that are set
+    # beside the oracle's
+    ctx = Context(dims, device=device)
+    ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
+                   sap_block=cfg["sap_block"], precision=MIXED)
+    ctx.load_gauge(U)
+    ctx.setup(cfg["seed"])
+    lam_v, V, _, _ = ctx.eigensolve(cfg["n_eig"], cfg["tol"], want_vectors=True)
+    ctx.close()
     return dict(gpu_s=statistics.median(times), max_resid=float(max(res)), converged=st["converged"],
-                n_eig=cfg["n_eig"], outer_iters=st["outer_iters"], solves=st["solves"])
+                n_eig=cfg["n_eig"], outer_iters=st["outer_iters"], solves=st["solves"]), (lam_v, V)
+
+
+def pairs_vs_oracle(lam, V, lam_o, V_o):
+    """How far the GPU's eigenpairs lie from the oracle's on the same field: the
+    largest eigenvalue difference relative to the largest |lambda| (both lists
+    sorted by value), and the smallest norm of a GPU eigenvector's projection on
+    the span of the oracle's eigenvectors (1 when the sets agree; basis-free, so
+    degenerate pairs compare too)."""
+    import numpy as np
+
+    lam, lam_o = np.sort(np.asarray(lam, float)), np.sort(np.asarray(lam_o, float))
+    if lam.shape != lam_o.shape:
+        return dict(error=f"{lam.size} GPU pairs against {lam_o.size} oracle pairs")
+    G = np.asarray(V).reshape(len(V), -1)
+    O = np.asarray(V_o).reshape(len(V_o), -1)
+    Qo, _ = np.linalg.qr(O.T)                 # orthonormal basis of the oracle's span
+    proj = np.linalg.norm(Qo.conj().T @ G.T, axis=0) / np.linalg.norm(G, axis=1)
+    return dict(max_rel_dlambda=float(np.max(np.abs(lam - lam_o)) / np.max(np.abs(lam_o))),
+                min_span_overlap=float(np.min(proj)), lambda_gpu=lam.tolist(), lambda_oracle=lam_o.tolist())
 
 
 # ---------------------------------------------------------------------------
@@ -633,10 +668,11 @@ def oracle_outer_iteration_s(name: str, iters: int):
     return (time.perf_counter() - t0) / iters
 
 
-def oracle_complete_small():
+def oracle_complete_small(vectors_path=None):
     """One complete oracle eigensolve (setup and Algorithm 1 with the library's
     default additions) of the 4^4 workload's 4 lowest pairs to 1e-10: its wall
-    time and work."""
+    time, work and eigenvalues; the eigenvectors go to `vectors_path` (.npy)
+    when one is given."""
     import numpy as np
 
     import synth
@@ -652,11 +688,13 @@ def oracle_complete_small():
                                      cfg["tol"], params)
     wall = time.perf_counter() - t0
     assert float(np.max(res)) <= cfg["tol"], res
+    if vectors_path:
+        np.save(vectors_path, np.asarray(V))
     return dict(wall_s=wall, n_eig=cfg["n_eig"], sweeps=st["sweeps"], solves=st["solves"],
-                outer_iters=st["outer_iters"], max_res=float(np.max(res)))
+                outer_iters=st["outer_iters"], max_res=float(np.max(res)), lam=np.asarray(lam).tolist())
 
 
-def oracle_baseline(c_big=None):
+def oracle_baseline(c_big=None, vectors_path=None):
     """The FP64 CPU oracle, measured: a complete oracle eigensolve of the 4^4
     workload (4 pairs to 1e-10, about 40 s), scaled to the 20 pairs of the 16^3 x
     32 benchmark field by the oracle's own measured cost of one outer FGMRES
@@ -668,7 +706,7 @@ def oracle_baseline(c_big=None):
     use one core, its LAPACK calls more)."""
     c0 = time.process_time()
     t0 = time.perf_counter()
-    small = oracle_complete_small()
+    small = oracle_complete_small(vectors_path)
     c_small = oracle_outer_iteration_s("dense_4x4x4x4", 6)
     if c_big is None:
         c_big = oracle_outer_iteration_s("bench_16x16x16x32", 1)
@@ -683,9 +721,11 @@ def oracle_baseline(c_big=None):
                 sample_seconds=wall, complete_4x4x4x4=small, outer_iteration_s=dict(small=c_small, bench=c_big))
 
 
-def oracle_baseline_subprocess():
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample"], capture_output=True,
-                       text=True, timeout=1800)
+def oracle_baseline_subprocess(vectors_path=None):
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample"]
+    if vectors_path:
+        cmd += ["--oracle-vectors", vectors_path]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=1800)
     if r.returncode != 0:
         return dict(kind="oracle", error=r.stderr[-500:])
     return json.loads(r.stdout.strip().splitlines()[-1])
@@ -900,9 +940,10 @@ def main():
     ap.add_argument("--batch-study", action="store_true",
                     help="16 shifts x 12 Z2 right-hand sides on six fields (8^4, 12^3x24, 16^3x32) with mgeig_solve_batch")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-vectors", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
-        print(json.dumps(oracle_baseline()))
+        print(json.dumps(oracle_baseline(vectors_path=args.oracle_vectors)))
         return
     if args.profile_case:
         profile_case(args.profile_case)
