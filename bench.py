@@ -434,6 +434,7 @@ def run_gpu(args):
         if cs:
             small["oracle_s"] = cs["wall_s"]
             small["oracle_over_gpu"] = cs["wall_s"] / small["gpu_s"]
+        if cs and small_pairs is not None:
             # the error of the GPU's result against the FP64 oracle's
             try:
                 small["vs_oracle"] = pairs_vs_oracle(small_pairs[0], small_pairs[1], cs["lam"], np.load(vec_path))
@@ -595,15 +596,20 @@ def small_field(flush, device):
         times.append(e0.elapsed_time(e1) / 1e3)
     # the same eigensolve once more, untimed, for the eigenvectors that are set
     # beside the oracle's
-    ctx = Context(dims, device=device)
-    ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
-                   sap_block=cfg["sap_block"], precision=MIXED)
-    ctx.load_gauge(U)
-    ctx.setup(cfg["seed"])
-    lam_v, V, _, _ = ctx.eigensolve(cfg["n_eig"], cfg["tol"], want_vectors=True)
-    ctx.close()
-    return dict(gpu_s=statistics.median(times), max_resid=float(max(res)), converged=st["converged"],
-                n_eig=cfg["n_eig"], outer_iters=st["outer_iters"], solves=st["solves"]), (lam_v, V)
+    out = dict(gpu_s=statistics.median(times), max_resid=float(max(res)), converged=st["converged"],
+               n_eig=cfg["n_eig"], outer_iters=st["outer_iters"], solves=st["solves"])
+    try:
+        ctx = Context(dims, device=device)
+        ctx.set_params(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
+                       sap_block=cfg["sap_block"], precision=MIXED)
+        ctx.load_gauge(U)
+        ctx.setup(cfg["seed"])
+        lam_v, V, _, _ = ctx.eigensolve(cfg["n_eig"], cfg["tol"], want_vectors=True)
+        ctx.close()
+        return out, (lam_v, V)
+    except Exception as e:  # the timed numbers above stand without the comparison
+        out["vs_oracle"] = dict(error=repr(e)[:300])
+        return out, None
 
 
 def pairs_vs_oracle(lam, V, lam_o, V_o):
