@@ -2,8 +2,12 @@
 against dense linear algebra on small lattices: P^dag P = 1, gamma5 P = P gamma5^c
 (Eq. 2.4), the per-direction coarse blocks summed = P^dag D P (Eq. 2.5),
 gamma5^c D_c Hermitian (Eq. 2.5), equal coarse corrections for D and Q (Eq. 2.6),
-block MR converging to the exact Dirichlet block solve, and GMRES/FGMRES reaching
-the dense solution."""
+block MR converging to the exact Dirichlet block solve, one MR step minimising
+each block's residual, SAP with exact blocks = multiplicative Schwarz in the
+colour order 0, 1, the two-grid cycle = exact coarse correction followed by the
+post-smoother (SAP on D_sigma with right-hand side gamma5 r, or GMRES(k) as the
+least-squares minimiser over the Krylov space; deflated and plain coarse solves
+alike), and GMRES/FGMRES reaching the dense solution."""
 import numpy as np
 import pytest
 
@@ -150,3 +154,131 @@ def test_deflated_preconditioner_solves_the_deflation_space_exactly(setup4):
     out2 = M(r2)
     assert np.abs(B.seen - r2).max() < 1e-12 * np.abs(r2).max()
     assert np.abs(out2 - 2.0 * r2).max() < 1e-12 * np.abs(r2).max()
+
+
+def _dense_dsigma(op, Dmat, sigma):
+    g5 = np.tile(np.repeat(dirac.GAMMA5_DIAG, 3), Dmat.shape[0] // 12)
+    return Dmat - sigma * np.diag(g5), g5
+
+
+def _masked_solve(Ds, mask, r):
+    """The exact Dirichlet solve on every block of one colour (the blocks of a
+    colour do not touch, so the masked system is block diagonal)."""
+    m = mask.ravel() > 0
+    out = np.zeros(r.size, dtype=complex)
+    out[m] = np.linalg.solve(Ds[np.ix_(m, m)], r.ravel()[m])
+    return out
+
+
+def test_one_mr_step_minimises_each_block_residual(setup4):
+    """One block MR step from e = 0 takes e_B = alpha_B r_B with the alpha_B that
+    minimises ||r_B - alpha A_BB r_B|| on every block B of the colour: the
+    residual left on B is orthogonal to A_BB r_B, and nudging alpha_B in any
+    complex direction raises it."""
+    op, W, P, Dmat, Pmat = setup4
+    sap = mg.SAP(op, (2, 2, 2, 2))
+    sigma = 0.05
+    Ds, _ = _dense_dsigma(op, Dmat, sigma)
+    r = synth.gaussian_vectors(DIMS, 1, 11)[0]
+    for colour in (0, 1):
+        mask = np.broadcast_to(sap.mask[colour], r.shape)
+        e = sap.block_mr(r, colour, sigma, 1).ravel()
+        m = mask.ravel() > 0
+        A = Ds[np.ix_(m, m)]                       # block diagonal over the colour's blocks
+        rb, eb = r.ravel()[m], e[m]
+        assert np.abs(e[~m]).max() == 0.0           # nothing written outside the colour
+        blk = _block_index(mask, sap)[m]            # block id of each masked unknown
+        for b in np.unique(blk):
+            s = blk == b
+            Arb = (A @ np.where(s, rb, 0))[s]
+            alpha = np.vdot(rb[s], eb[s]) / np.vdot(rb[s], rb[s])
+            assert np.abs(eb[s] - alpha * rb[s]).max() < 1e-13 * np.abs(eb[s]).max()
+            left = rb[s] - alpha * Arb
+            assert abs(np.vdot(Arb, left)) < 1e-12 * np.linalg.norm(Arb) * np.linalg.norm(rb[s])
+            for d in (1e-3, 1e-3j, -1e-3, -1e-3j):
+                assert np.linalg.norm(rb[s] - alpha * (1 + d) * Arb) > np.linalg.norm(left)
+
+
+def _block_index(mask, sap):
+    """Block index (0 .. nblk-1) of every entry of a (T, Z, Y, X, 4, 3) field."""
+    dims = sap.op.dims
+    idx = sum(mg.site_coordinate(dims, mu) // sap.block[mu] * int(np.prod([dims[n] // sap.block[n] for n in range(mu)]))
+              for mu in range(4))
+    return np.broadcast_to(idx, mask.shape).ravel()
+
+
+def test_sap_cycles_with_exact_blocks_are_multiplicative_schwarz(setup4):
+    """With the block MR run to convergence, `cycles` SAP cycles are the
+    multiplicative Schwarz iteration on D_sigma: per cycle, colour 0 then colour
+    1, x <- x + M_c (b - D_sigma x) with M_c the exact Dirichlet solve on the
+    colour's blocks."""
+    op, W, P, Dmat, Pmat = setup4
+    sap = mg.SAP(op, (2, 2, 2, 2))
+    sigma = -0.03
+    Ds, _ = _dense_dsigma(op, Dmat, sigma)
+    b = synth.gaussian_vectors(DIMS, 1, 12)[0]
+    x0 = synth.gaussian_vectors(DIMS, 1, 13)[0]
+    got = sap.smooth(b, x0, sigma, 2, 300).ravel()
+    x = x0.ravel().astype(complex)
+    for _ in range(2):
+        for colour in (0, 1):
+            mask = np.broadcast_to(sap.mask[colour], b.shape)
+            x = x + _masked_solve(Ds, mask, b.ravel() - Ds @ x)
+    assert np.abs(got - x).max() < 1e-9 * np.abs(x).max()
+    # the colour order matters: the other order gives another result
+    y = x0.ravel().astype(complex)
+    for colour in (1, 0):
+        mask = np.broadcast_to(sap.mask[colour], b.shape)
+        y = y + _masked_solve(Ds, mask, b.ravel() - Ds @ y)
+    one = sap.smooth(b, x0, sigma, 1, 300).ravel()
+    assert np.abs(one - y).max() > 1e-3 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("deflate", [False, True])
+def test_two_grid_is_exact_coarse_correction_then_sap(setup4, deflate):
+    """Eq. 2.3 with mu = 0, nu = 1 and exact pieces: B r = S(x) with
+    x = P (P^dag (Q - sigma) P)^-1 P^dag r, then one SAP cycle (exact blocks) on
+    D_sigma z = gamma5 r from z = x.  With the coarse GMRES run to convergence
+    the deflated and the plain coarse solve give the same B r (the deflation
+    is exact on span(W))."""
+    op, W, P, Dmat, Pmat = setup4
+    sigma = 0.04
+    Ds, g5 = _dense_dsigma(op, Dmat, sigma)
+    Qs = g5[:, None] * Dmat - sigma * np.eye(Dmat.shape[0])
+    params = dict(mg.DEFAULT_PARAMS, agg=AGG, ntv=NTV, sap_block=(2, 2, 2, 2), sap_cycles=1, sap_mr_iters=300,
+                  coarse_tol=1e-14, coarse_restart=60, coarse_maxiter=600, coarse_deflate=deflate)
+    B = mg.TwoGrid(op, W, params)
+    r = synth.gaussian_vectors(DIMS, 1, 14)[0]
+    got = B(r, sigma).ravel()
+    x = Pmat @ np.linalg.solve(Pmat.conj().T @ Qs @ Pmat, Pmat.conj().T @ r.ravel())
+    g5r = g5 * r.ravel()
+    for colour in (0, 1):
+        mask = np.broadcast_to(B.sap.mask[colour], r.shape)
+        x = x + _masked_solve(Ds, mask, g5r - Ds @ x)
+    assert np.abs(got - x).max() < 1e-9 * np.abs(x).max()
+
+
+def test_two_grid_gmres_smoother_minimises_over_the_krylov_space(setup4):
+    """The GMRES(k) post-smoother: one step from the coarse correction x adds
+    the e in K_k(Q - sigma, r - (Q - sigma) x) of least residual, the
+    least-squares solution over the Krylov space's monomial basis."""
+    op, W, P, Dmat, Pmat = setup4
+    sigma = 0.04
+    k = 4
+    Ds, g5 = _dense_dsigma(op, Dmat, sigma)
+    Qs = g5[:, None] * Dmat - sigma * np.eye(Dmat.shape[0])
+    params = dict(mg.DEFAULT_PARAMS, agg=AGG, ntv=NTV, smoother="gmres", smooth_steps=1, gmres_smooth_k=k,
+                  coarse_tol=1e-14, coarse_restart=60, coarse_maxiter=600, coarse_deflate=False)
+    B = mg.TwoGrid(op, W, params)
+    rf = synth.gaussian_vectors(DIMS, 1, 15)[0]
+    got = B(rf, sigma).ravel()
+    r = rf.ravel()
+    x = Pmat @ np.linalg.solve(Pmat.conj().T @ Qs @ Pmat, Pmat.conj().T @ r)
+    r0 = r - Qs @ x
+    K = [r0]
+    for _ in range(k - 1):
+        K.append(Qs @ K[-1])
+    K = np.array(K).T
+    y = np.linalg.lstsq(Qs @ K, r0, rcond=None)[0]
+    want = x + K @ y
+    assert np.abs(got - want).max() < 1e-8 * np.abs(want).max()
