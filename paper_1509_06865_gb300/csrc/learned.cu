@@ -47,7 +47,7 @@ constexpr int HX = BX + 2, HY = BY + 2, HZ = BZ + 2, HT = BT + 2;
 constexpr int HALO = HX * HY * HZ * HT;         // 864 rows
 constexpr int TAPS_PER_STAGE = 9;
 constexpr int CONV_THREADS = 128;
-constexpr int WG_BOXES = 8;                     // boxes per weight-gradient CTA
+constexpr int WG_BOXES = 16;                    // boxes per weight-gradient CTA
 constexpr float GELU_C = 0.7978845608028654f;   // sqrt(2 / pi)
 constexpr float GELU_A = 0.044715f;
 
@@ -143,19 +143,30 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __nv_bfloat16 *halo = reinterpret_cast<__nv_bfloat16 *>(smem);              // [HALO][32]
     __nv_bfloat16 *wst = halo + (size_t)HALO * NC;                              // [9][32][32]
+    static_assert(HALO % 32 == 0, "the halo rows come in groups of 32");
     int field, o[4];
     box_origin(a.D, blockIdx.x, field, o);
-    // the box and its halo, 16-byte async copies, periodic wrap
-    for (int e = threadIdx.x; e < HALO * 4; e += blockDim.x) {
-        int h = e >> 2, ch = e & 3;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the box and its halo, 16-byte async copies, periodic wrap: warp w takes the
+    // groups of 32 rows w, w + 4, ...; each lane works out the global offset of
+    // one row of the group, then four lanes at a time copy a row's four chunks
+    // (64 contiguous bytes) with the offset taken from the lane that owns it
+    for (int r0 = 32 * w; r0 < HALO; r0 += CONV_THREADS) {
+        int h = r0 + lane;
         int x[4];
         x[0] = wrap(o[0] + h % HX - 1, a.D.L[0]); h /= HX;
         x[1] = wrap(o[1] + h % HY - 1, a.D.L[1]); h /= HY;
         x[2] = wrap(o[2] + h % HZ - 1, a.D.L[2]);
         x[3] = wrap(o[3] + h / HZ - 1, a.D.L[3]);
-        cp_async16(halo + swz(e >> 2, ch), a.in + site_index(a.D, field, x) * NC + ch * 8);
+        const long long off = (long long)site_index(a.D, field, x) * NC;
+        const int ch = lane & 3;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int src = 8 * k + (lane >> 2);
+            const long long o_src = __shfl_sync(0xffffffffu, off, src);
+            cp_async16(halo + swz(r0 + src, ch), a.in + o_src + ch * 8);
+        }
     }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float acc[2][4][4];
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
@@ -233,8 +244,9 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
 // dW[tap][o][i] += sum_s dz(s)[o] in(s + tap)[i] over WG_BOXES boxes of sites
 __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(LatDims D, int nboxes, const __nv_bfloat16 *in,
                                                              const __nv_bfloat16 *dz, float *dW) {
-    __shared__ __align__(16) __nv_bfloat16 xs[BOX * NC];   // in(s + tap) of the box's sites
-    __shared__ __align__(16) __nv_bfloat16 gs[BOX * NC];   // dz(s)
+    static_assert(BOX == CONV_THREADS, "one staged site per thread");
+    __shared__ __align__(16) __nv_bfloat16 xs[BOX * NC];   // in(s + tap) of the box's sites (swizzled rows)
+    __shared__ __align__(16) __nv_bfloat16 gs[BOX * NC];   // dz(s) (swizzled rows)
     __shared__ float red[4][NC * NC / 4];                  // warp partials, 1/4 at a time
     const int tap = blockIdx.y;
     int d[4];
@@ -247,17 +259,28 @@ __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(LatDims D, int nbox
         for (int nj = 0; nj < 4; ++nj) acc[mi][nj][0] = acc[mi][nj][1] = acc[mi][nj][2] = acc[mi][nj][3] = 0.f;
     for (int bb = 0; bb < WG_BOXES; ++bb) {
         const int b = blockIdx.x * WG_BOXES + bb;
-        if (b >= nboxes) break;
+        if (b >= nboxes) break;   // the same for the whole CTA
         int field, o[4];
         box_origin(D, b, field, o);
         __syncthreads();
-        for (int e = threadIdx.x; e < BOX * 4; e += blockDim.x) {
-            const int l = e >> 2, ch = e & 3;
+        // warp w stages sites 32 w .. 32 w + 31: each lane works out the offsets
+        // of one site, then four lanes at a time copy a site's four chunks
+        // (64 contiguous bytes) with the offsets taken from the lane that owns it
+        {
             int c[4], x[4], y[4];
-            local_coords(l, c);
+            local_coords(32 * w + lane, c);
             for (int k = 0; k < 4; ++k) { x[k] = o[k] + c[k]; y[k] = wrap(x[k] + d[k], D.L[k]); }
-            cp_async16(gs + (size_t)l * NC + ch * 8, dz + site_index(D, field, x) * NC + ch * 8);
-            cp_async16(xs + (size_t)l * NC + ch * 8, in + site_index(D, field, y) * NC + ch * 8);
+            const long long og = (long long)site_index(D, field, x) * NC;
+            const long long ox = (long long)site_index(D, field, y) * NC;
+            const int ch = lane & 3;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int src = 8 * k + (lane >> 2);
+                const long long g_off = __shfl_sync(0xffffffffu, og, src);
+                const long long x_off = __shfl_sync(0xffffffffu, ox, src);
+                cp_async16(gs + swz(32 * w + src, ch), dz + g_off + ch * 8);
+                cp_async16(xs + swz(32 * w + src, ch), in + x_off + ch * 8);
+            }
         }
         cp_async_wait_all();
         __syncthreads();
@@ -269,14 +292,12 @@ __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(LatDims D, int nbox
             // A (out x sites) from dz rows (sites x out), transposed: matrix j = (out 8 (j % 2), sites 8 (j / 2))
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi)
-                ldmatrix_x4_trans(af[mi], gs + (size_t)(s0 + (lane & 7) + 8 * (lane >> 4)) * NC + 16 * mi +
-                                              8 * ((lane >> 3) & 1));
+                ldmatrix_x4_trans(af[mi], gs + swz(s0 + (lane & 7) + 8 * (lane >> 4), 2 * mi + ((lane >> 3) & 1)));
 #pragma unroll
             for (int np = 0; np < 2; ++np) {
                 uint32_t bf[4];
                 // B (sites x in) from the rows of in(s + tap): matrix j = (sites 8 (j % 2), in 8 (2 np + j / 2))
-                ldmatrix_x4_trans(bf, xs + (size_t)(s0 + (lane & 7) + 8 * ((lane >> 3) & 1)) * NC + 16 * np +
-                                          8 * (lane >> 4));
+                ldmatrix_x4_trans(bf, xs + swz(s0 + (lane & 7) + 8 * ((lane >> 3) & 1), 2 * np + (lane >> 4)));
 #pragma unroll
                 for (int mi = 0; mi < 2; ++mi) {
                     mma16816(acc[mi][2 * np], af[mi], bf[0], bf[1]);
