@@ -67,6 +67,27 @@ def test_gradients_match_oracle():
     ctx.close()
 
 
+def test_forward_and_gradients_on_an_uneven_lattice():
+    """8 x 4 x 4 x 6, batch 3: the halo wraps onto its own box in y and z, three
+    boxes in t, and the weight gradient spreads the 18 boxes over two CTAs per
+    tap, the second one ragged (2 of 16)."""
+    dims = (8, 4, 4, 6)
+    ctx = ctx_for(dims, agg=(2, 2, 2, 2), sap_block=(2, 2, 2, 3), n_tv=8)
+    ctx.net_init(13)
+    W = ctx.net_get_weights()
+    r = synth.gaussian_vectors(dims, 1, 3)[0]
+    assert norm_rel_err(ctx.net_apply(r), L.smoother(oracle_weights(W), r)) < 3e-2
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(3,) + tuple(dims[::-1]) + (24,))
+    t = 0.3 * rng.normal(size=x.shape)
+    loss, G = ctx.net_loss_grads(x, t)
+    lo, Go = L.loss_and_grads(oracle_weights(W), x, t)
+    assert abs(loss - lo) <= 2e-2 * lo
+    for l, g in enumerate(oracle_weights(G)):
+        assert norm_rel_err(g, Go[l]) < 5e-2, l
+    ctx.close()
+
+
 @pytest.fixture(scope="module")
 def trained():
     dims = (8, 8, 8, 8)
