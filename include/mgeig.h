@@ -214,6 +214,15 @@ void mgeig_destroy(mgeig_ctx *ctx);
  * direction, 2 <= n_tv <= 24, bc = +-1, positive iteration counts. */
 int mgeig_set_params(mgeig_ctx *ctx, const mgeig_params *p);
 
+/* The checks of mgeig_create (lattice) and mgeig_set_params (parameters) for
+ * the lattice dims without a context: MGEIG_OK if a context of that lattice
+ * would accept p, else MGEIG_EINVAL.  Host only: no device call, no allocation,
+ * usable without a GPU.  Besides the checks listed above: aggregate and SAP
+ * block volumes <= 1024, n_tv <= 6 x aggregate volume, 16-bit coarse links and
+ * the learned smoother only with MGEIG_MIXED, the learned smoother only on
+ * extents divisible by 4 x 4 x 4 x 2, 0 < barrier_timeout <= 60. */
+int mgeig_check_params(const int dims[4], const mgeig_params *p);
+
 /* Copy a host gauge field (layout above) to the device and build the clover
  * term from it (four-leaf clover, FP64, Sec. 2 / the operator above). */
 int mgeig_load_gauge(mgeig_ctx *ctx, const double *U);

@@ -77,6 +77,7 @@ def load():
         "mgeig_create": (I, [C.POINTER(P), C.POINTER(C.c_int), I]),
         "mgeig_destroy": (None, [P]),
         "mgeig_set_params": (I, [P, C.POINTER(Params)]),
+        "mgeig_check_params": (I, [C.POINTER(C.c_int), C.POINTER(Params)]),
         "mgeig_load_gauge": (I, [P, P]),
         "mgeig_load_gauge_dev": (I, [P, P]),
         "mgeig_get_clover": (I, [P, P]),
@@ -139,6 +140,25 @@ def _c128(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
+def make_params(**kw) -> Params:
+    """The library defaults with the given fields replaced."""
+    lib = load()
+    p = Params()
+    lib.mgeig_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k in ("bc", "agg", "sap_block"):
+            setattr(p, k, (C.c_int * 4)(*v))
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def check_params(dims, **kw) -> int:
+    """mgeig_check_params: 0 if a context of lattice dims (Lx, Ly, Lz, Lt) would
+    accept these parameters, else the status code.  Needs no GPU."""
+    return load().mgeig_check_params((C.c_int * 4)(*dims), C.byref(make_params(**kw)))
+
+
 def solve_batch(ctxs, sigmas, rhs, tol=1e-10):
     """(Q - sigma_s) x = b_j for every context (rhs[k]: [nrhs, ...] spinors of context k's
     lattice, the same nrhs for all): list of arrays [nsig, nrhs, ...] and the summed stats."""
@@ -192,13 +212,7 @@ class Context:
 
     # ---- configuration -------------------------------------------------
     def set_params(self, **kw):
-        p = Params()
-        self.lib.mgeig_default_params(C.byref(p))
-        for k, v in kw.items():
-            if k in ("bc", "agg", "sap_block"):
-                setattr(p, k, (C.c_int * 4)(*v))
-            else:
-                setattr(p, k, v)
+        p = make_params(**kw)
         self._check("mgeig_set_params", self.lib.mgeig_set_params(self._h, C.byref(p)))
         self.params = p
 

@@ -32,13 +32,26 @@ bool divides_all(const int *blk, const int *dims) {
     return true;
 }
 
-int validate(const Ctx &c, const mgeig_params &p) {
+// the lattice checks of mgeig_create: every extent >= 2, 12 V below 2^31
+int check_dims(const int dims[4], long long *V_out = nullptr) {
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2) return MGEIG_EINVAL;
+        V *= dims[mu];
+    }
+    if (V >= (1LL << 31) / 12) return MGEIG_EINVAL;
+    if (V_out) *V_out = V;
+    return MGEIG_OK;
+}
+
+// the parameter checks of mgeig_set_params for a lattice of extents dims
+int validate(const int dims[4], const mgeig_params &p) {
     for (int mu = 0; mu < 4; ++mu)
         if (p.bc[mu] != 1 && p.bc[mu] != -1) return MGEIG_EINVAL;
-    if (!divides_all(p.agg, c.dims) || !divides_all(p.sap_block, c.dims)) return MGEIG_EINVAL;
+    if (!divides_all(p.agg, dims) || !divides_all(p.sap_block, dims)) return MGEIG_EINVAL;
     int avol = 1, bvol = 1;
     for (int mu = 0; mu < 4; ++mu) {
-        const int nb = c.dims[mu] / p.sap_block[mu];
+        const int nb = dims[mu] / p.sap_block[mu];
         if (nb < 2 || nb % 2) return MGEIG_EINVAL;
         avol *= p.agg[mu];
         bvol *= p.sap_block[mu];
@@ -68,7 +81,7 @@ int validate(const Ctx &c, const mgeig_params &p) {
     if (!(p.coarse_tol >= 0) || !(p.solve_tol > 0)) return MGEIG_EINVAL;
     if (p.precision != MGEIG_FP64 && p.precision != MGEIG_MIXED) return MGEIG_EINVAL;
     if (p.smoother != MGEIG_SAP && p.smoother != MGEIG_GMRES && p.smoother != MGEIG_LEARNED) return MGEIG_EINVAL;
-    if (p.smoother == MGEIG_LEARNED && (p.precision != MGEIG_MIXED || !net_supported(c))) return MGEIG_EINVAL;
+    if (p.smoother == MGEIG_LEARNED && (p.precision != MGEIG_MIXED || !net_supported_dims(dims))) return MGEIG_EINVAL;
     if (p.max_sweeps < 1 || p.n_guard < -1) return MGEIG_EINVAL;
     return MGEIG_OK;
 }
@@ -144,11 +157,7 @@ int mgeig_create(mgeig_ctx **out, const int dims[4], int device) {
     if (!out || !dims) return MGEIG_EINVAL;
     *out = nullptr;
     long long V = 1;
-    for (int mu = 0; mu < 4; ++mu) {
-        if (dims[mu] < 2) return MGEIG_EINVAL;
-        V *= dims[mu];
-    }
-    if (V >= (1LL << 31) / 12) return MGEIG_EINVAL;
+    if (check_dims(dims, &V) != MGEIG_OK) return MGEIG_EINVAL;
     mgeig_ctx *ctx = new (std::nothrow) mgeig_ctx();
     if (!ctx) return MGEIG_ENOMEM;
     Ctx &c = ctx->c;
@@ -201,10 +210,16 @@ void mgeig_destroy(mgeig_ctx *ctx) {
     delete ctx;
 }
 
+int mgeig_check_params(const int dims[4], const mgeig_params *p) {
+    if (!dims || !p) return MGEIG_EINVAL;
+    const int rc = check_dims(dims);
+    return rc != MGEIG_OK ? rc : validate(dims, *p);
+}
+
 int mgeig_set_params(mgeig_ctx *ctx, const mgeig_params *p) {
     if (!ctx || !p) return MGEIG_EINVAL;
     return guarded(ctx, [&](Ctx &c) {
-        int rc = validate(c, *p);
+        int rc = validate(c.dims, *p);
         if (rc != MGEIG_OK) return rc;
         sync(c);
         mg_free(c);

@@ -264,7 +264,8 @@ void interp_f64(Ctx &c, void *const *out64);
 int grid_for(size_t n, int threads);
 
 // ----- the learned smoother (learned.cu) -----
-bool net_supported(const Ctx &c);   // lattice extents divisible by the 4 x 4 x 4 x 2 box
+bool net_supported_dims(const int dims[4]);   // extents divisible by the 4 x 4 x 4 x 2 box
+bool net_supported(const Ctx &c);             // the same for the context's lattice
 void net_init(Ctx &c, uint64_t seed);
 void net_set_weights(Ctx &c, const float *host);   // [3][81][32][32] FP32
 void net_get_weights(Ctx &c, float *host);

@@ -455,9 +455,10 @@ static LatDims lat(const Ctx &c) {
     return D;
 }
 
-bool net_supported(const Ctx &c) {
-    return c.dims[0] % BX == 0 && c.dims[1] % BY == 0 && c.dims[2] % BZ == 0 && c.dims[3] % BT == 0;
+bool net_supported_dims(const int dims[4]) {
+    return dims[0] % BX == 0 && dims[1] % BY == 0 && dims[2] % BZ == 0 && dims[3] % BT == 0;
 }
+bool net_supported(const Ctx &c) { return net_supported_dims(c.dims); }
 
 static Net &net(Ctx &c) {
     MG_REQUIRE(net_supported(c), MGEIG_EINVAL);

@@ -67,3 +67,47 @@ def test_stats_struct_matches_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     order = re.findall(r"([a-z0-9_]+)\s*;", body)
     assert order == [f for f, _ in Stats._fields_]
+
+
+def test_parameter_checks_without_a_gpu(lib):
+    """mgeig_check_params: the lattice and parameter checks of mgeig_create and
+    mgeig_set_params, host only.  The defaults pass on the benchmark lattices;
+    every documented rule rejects its violation; the edge values pass."""
+    from paper_1509_06865_gb300 import LEARNED, LINKS_BF16, check_params
+    ok = [((16, 16, 16, 32), {}), ((32, 32, 32, 64), {}), ((8, 8, 8, 8), {}),
+          ((4, 4, 4, 4), dict(agg=(2, 2, 2, 2), sap_block=(2, 2, 2, 2), n_tv=8)),
+          ((12, 12, 12, 24), dict(agg=(3, 3, 3, 3), sap_block=(3, 3, 3, 3))),     # SAP: 4 x 4 x 4 x 8 blocks
+          ((8, 4, 4, 6), dict(agg=(2, 2, 2, 2), sap_block=(2, 2, 2, 3), n_tv=8)),
+          ((6, 8, 8, 8), dict(agg=(3, 4, 4, 4), sap_block=(3, 4, 4, 4))),
+          ((16, 16, 16, 32), dict(p_modes=-1, n_guard=-1, barrier_timeout=60.0, blas_blocks=64, n_tv=24)),
+          ((16, 16, 16, 32), dict(coarse_links=LINKS_BF16)),
+          ((16, 16, 16, 32), dict(smoother=LEARNED)),
+          ((16, 16, 16, 32), dict(bc=(1, 1, 1, -1), sap_cycles=0, smooth_steps=0, setup_iters=0))]
+    for dims, kw in ok:
+        assert check_params(dims, **kw) == 0, (dims, kw)
+    bad = [((1, 16, 16, 32), {}),                                        # an extent below 2
+           ((1024, 1024, 1024, 2), {}),                                  # 12 V beyond 2^31
+           ((12, 12, 12, 24), {}),                                       # 4^4 SAP blocks: 3 per direction, odd
+           ((16, 16, 16, 32), dict(agg=(3, 4, 4, 4))),                   # aggregate does not divide
+           ((16, 16, 16, 32), dict(sap_block=(16, 4, 4, 4))),            # one SAP block in x
+           ((32, 32, 32, 64), dict(agg=(8, 8, 8, 4))),                   # aggregate volume 2048 > 1024
+           ((16, 16, 16, 32), dict(n_tv=25)), ((16, 16, 16, 32), dict(n_tv=1)),
+           ((16, 16, 16, 32), dict(agg=(1, 1, 1, 2), n_tv=20)),          # n_tv > 6 x aggregate volume
+           ((16, 16, 16, 32), dict(bc=(1, 1, 1, 0))),
+           ((16, 16, 16, 32), dict(sap_mr_iters=0)), ((16, 16, 16, 32), dict(gmres_smooth_k=0)),
+           ((16, 16, 16, 32), dict(outer_restart=0)), ((16, 16, 16, 32), dict(outer_restart=101)),
+           ((16, 16, 16, 32), dict(coarse_restart=100000)), ((16, 16, 16, 32), dict(coarse_maxiter=0)),
+           ((16, 16, 16, 32), dict(coarse_deflate=2)), ((16, 16, 16, 32), dict(shift_floor=1.0)),
+           ((16, 16, 16, 32), dict(ritz_keep=float("nan"))), ((16, 16, 16, 32), dict(fine_deflate_radius=float("inf"))),
+           ((16, 16, 16, 32), dict(coarse_links=LINKS_BF16, precision=0)),   # 16-bit links need MIXED
+           ((16, 16, 16, 32), dict(smoother=LEARNED, precision=0)),          # the network needs MIXED
+           ((6, 8, 8, 8), dict(agg=(3, 4, 4, 4), sap_block=(3, 4, 4, 4), smoother=LEARNED)),  # 6 % 4 != 0
+           ((16, 16, 16, 32), dict(barrier_timeout=0.0)), ((16, 16, 16, 32), dict(barrier_timeout=61.0)),
+           ((16, 16, 16, 32), dict(p_modes=0)), ((16, 16, 16, 32), dict(blas_blocks=65)),
+           ((16, 16, 16, 32), dict(solve_tol=0.0)), ((16, 16, 16, 32), dict(precision=2)),
+           ((16, 16, 16, 32), dict(smoother=3)), ((16, 16, 16, 32), dict(max_sweeps=0)),
+           ((16, 16, 16, 32), dict(n_guard=-2))]
+    for dims, kw in bad:
+        assert check_params(dims, **kw) == -1, (dims, kw)
+    p = (ctypes.c_int * 4)(16, 16, 16, 32)
+    assert lib.mgeig_check_params(None, None) == -1 and lib.mgeig_check_params(p, None) == -1
