@@ -111,3 +111,21 @@ def test_parameter_checks_without_a_gpu(lib):
         assert check_params(dims, **kw) == -1, (dims, kw)
     p = (ctypes.c_int * 4)(16, 16, 16, 32)
     assert lib.mgeig_check_params(None, None) == -1 and lib.mgeig_check_params(p, None) == -1
+
+
+def test_every_workload_passes_the_library_checks(lib):
+    """The synthetic workloads (workloads.json) and the uneven field sizes of
+    the batched solves are accepted by the library's own lattice and parameter
+    checks, in both precisions, before any GPU sees them."""
+    import json
+    from paper_1509_06865_gb300 import FP64, MIXED, check_params
+    w = json.load(open(os.path.join(ROOT, "workloads.json")))
+    for name, cfg in w.items():
+        if name.startswith("_"):
+            continue
+        for prec in (FP64, MIXED):
+            kw = dict(m0=cfg["m0"], csw=cfg["csw"], bc=cfg["bc"], agg=cfg["agg"], n_tv=cfg["n_tv"],
+                      sap_block=cfg["sap_block"], precision=prec)
+            assert check_params(cfg["dims"], **kw) == 0, (name, prec)
+    for dims, sap in (((8, 8, 8, 8), (4, 4, 4, 4)), ((12, 12, 12, 24), (3, 3, 3, 3)), ((16, 16, 16, 32), (4, 4, 4, 4))):
+        assert check_params(dims, n_tv=20, precision=MIXED, sap_block=sap) == 0, dims
