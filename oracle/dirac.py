@@ -189,3 +189,33 @@ def dot(a: np.ndarray, b: np.ndarray) -> complex:
 
 def norm(a: np.ndarray) -> float:
     return float(np.sqrt(np.real(np.vdot(a, a))))
+
+
+def apply_at_site(U: np.ndarray, psi: np.ndarray, site, m0: float, csw: float, bc=(1, 1, 1, 1),
+                  sigma: float = 0.0, form: str = "Q") -> np.ndarray:
+    """One site of (Q - sigma) psi (form "Q") or (D - sigma gamma5) psi (form "D"),
+    for lattices too large for the whole-lattice operator above.
+
+    The operator is local: the hopping terms at x read psi(x +- mu) and the
+    clover term the links of the leaves around x, all on sites within one step
+    of x in every direction.  So the value at x is the whole-lattice operator
+    of this module applied to the 3^4 patch of links and spinors around x,
+    read at the patch centre; the patch copies psi(x +- mu) with the boundary
+    phase bc[mu] already applied where the step crosses the lattice edge (the
+    patch itself is never wrapped at its centre).  site = (x, y, z, t); U and psi
+    in this module's layout (T, Z, Y, X, ...).  Returns the (4, 3) spinor.
+    """
+    dims = (U.shape[3], U.shape[2], U.shape[1], U.shape[0])     # (Lx, Ly, Lz, Lt)
+    idx, phase = [], []
+    for mu in range(4):
+        c = np.arange(site[mu] - 1, site[mu] + 2)
+        idx.append(c % dims[mu])
+        phase.append(np.where((c < 0) | (c >= dims[mu]), bc[mu], 1).astype(float))
+    it, iz, iy, ix = idx[3], idx[2], idx[1], idx[0]
+    Up = U[np.ix_(it, iz, iy, ix)]
+    pp = psi[np.ix_(it, iz, iy, ix)].copy()
+    pp *= (phase[3][:, None, None, None] * phase[2][None, :, None, None] * phase[1][None, None, :, None]
+           * phase[0][None, None, None, :])[..., None, None]
+    op = WilsonClover(Up, m0, csw, bc=(1, 1, 1, 1))
+    out = op.Q_sigma(pp, sigma) if form == "Q" else op.D_sigma(pp, sigma)
+    return out[1, 1, 1, 1]

@@ -107,3 +107,20 @@ def test_clover_single_deformed_link_by_hand():
 def test_clover_vanishes_for_unit_links():
     A = dirac.clover_matrix(synth.unit_gauge((2, 2, 2, 2)), 1.9)
     assert np.abs(A).max() == 0
+
+
+def test_operator_at_one_site_equals_the_whole_lattice_operator():
+    """dirac.apply_at_site (the 3^4 patch around a site, for sampled checks on
+    lattices too large for the whole-lattice operator) agrees with the
+    whole-lattice Q - sigma and D - sigma gamma5 at every site of an uneven,
+    partly antiperiodic lattice, the edge sites included."""
+    import itertools
+    dims, bc = (4, 6, 4, 4), (-1, 1, 1, -1)
+    U = synth.gauge_field(dims, 0.3, 5)
+    psi = synth.gaussian_vectors(dims, 1, 6)[0]
+    op = dirac.WilsonClover(U, -0.3, 1.7, bc=bc)
+    for form, sigma in (("Q", 0.07), ("D", -0.02)):
+        full = op.Q_sigma(psi, sigma) if form == "Q" else op.D_sigma(psi, sigma)
+        for x, y, z, t in itertools.product(*(range(L) for L in dims)):
+            v = dirac.apply_at_site(U, psi, (x, y, z, t), -0.3, 1.7, bc, sigma, form)
+            assert np.abs(v - full[t, z, y, x]).max() <= 1e-14 * np.abs(full).max()
